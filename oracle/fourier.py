@@ -1,0 +1,100 @@
+"""Closed-form Fourier-mode solution of the collocation stepping (second,
+independent oracle for periodic constant-coefficient A; test infrastructure
+only).
+
+On a periodic grid every stencil operator is diagonal in the discrete Fourier
+basis: A e_k = sigma(k) e_k with e_k(x_j) = exp(2 pi i k j / n).  For one mode
+with z = dT sigma(k), the stepping of eq. (seq_collocation_problem) reads
+    (I - z Q) uhat_1 = uhat_0 1_M,   (I - z Q) uhat_l = uhat_{l-1,M} 1_M,
+so with s(z) = (I - z Q)^{-1} 1_M and R(z) = s_M(z) (the stability function
+of the collocation method),
+    uhat_{l,m} = s_m(z) R(z)^{l-1} uhat_0,   l = 1..L.
+"""
+import numpy as np
+
+
+def symbol_d1(n, length=1.0, order=2):
+    """Eigenvalues of the periodic central first derivative, mode k = 0..n-1."""
+    h = length / n
+    th = 2 * np.pi * np.arange(n) / n
+    if order == 2:
+        return 1j * np.sin(th) / h
+    return 1j * (8 * np.sin(th) - np.sin(2 * th)) / (6 * h)
+
+
+def symbol_d2(n, length=1.0, order=2):
+    """Eigenvalues of the periodic central second derivative."""
+    h = length / n
+    th = 2 * np.pi * np.arange(n) / n
+    if order == 2:
+        return (2 * np.cos(th) - 2) / h ** 2
+    return (-2 * np.cos(2 * th) + 32 * np.cos(th) - 30) / (12 * h ** 2)
+
+
+def symbol(prob):
+    """sigma(k) for A = nu Lap - c . grad; shape (nx,) in 1D, (ny, nx) in 2D
+    (matching numpy.fft.fft2 of a field stored as [iy, ix])."""
+    nx, lx, order = prob["nx"], prob.get("lx", 1.0), prob["order"]
+    sx = prob["nu"] * symbol_d2(nx, lx, order) - prob.get("cx", 0.0) * symbol_d1(nx, lx, order)
+    if prob["dim"] == 1:
+        return sx
+    ny, ly = prob["ny"], prob.get("ly", 1.0)
+    sy = prob["nu"] * symbol_d2(ny, ly, order) - prob.get("cy", 0.0) * symbol_d1(ny, ly, order)
+    return sy[:, None] + sx[None, :]
+
+
+def stage_vector(z, Q):
+    """s(z) = (I - z Q)^{-1} 1_M for an array of z; shape z.shape + (M,)."""
+    z = np.asarray(z, dtype=np.complex128)
+    M = Q.shape[0]
+    Az = np.eye(M) - z[..., None, None] * Q
+    rhs = np.ones(z.shape + (M, 1), dtype=np.complex128)
+    return np.linalg.solve(Az, rhs)[..., 0]
+
+
+def stability_function(z, Q):
+    """R(z) = e_M^T (I - z Q)^{-1} 1_M."""
+    return stage_vector(z, Q)[..., -1]
+
+
+def _fwd(u, prob):
+    if prob["dim"] == 1:
+        return np.fft.fft(u)
+    return np.fft.fft2(u.reshape(prob["ny"], prob["nx"]))
+
+
+def _inv(uh, prob):
+    if prob["dim"] == 1:
+        return np.fft.ifft(uh)
+    return np.fft.ifft2(uh).reshape(-1)
+
+
+def modal_solution(u0, prob, Q, dT, L, blocks=None):
+    """u of shape (L, M, N) from uhat_{l,m} = s_m R^{l-1} uhat_0.
+
+    ``blocks`` (optional list of (l, m) pairs, 0-based) restricts the output
+    to those blocks: returns a dict {(l, m): u_lm}."""
+    z = dT * symbol(prob)
+    s = stage_vector(z, Q)
+    R = s[..., -1]
+    u0h = _fwd(np.asarray(u0, np.float64), prob)
+    M = Q.shape[0]
+    if blocks is not None:
+        return {(l, m): _inv(s[..., m] * R ** l * u0h, prob).real for (l, m) in blocks}
+    N = np.asarray(u0).shape[0]
+    u = np.empty((L, M, N))
+    for l in range(L):
+        Rl = R ** l
+        for m in range(M):
+            u[l, m] = _inv(s[..., m] * Rl * u0h, prob).real
+    return u
+
+
+def contraction_factor(z, alpha, L, Q):
+    """Per-mode error factor of one Richardson iteration with exact inner
+    solves: -alpha R^L / (1 - alpha R^L).  Derived from eqs. (prec) and
+    (Riteration): (C_alpha - C) e^k lives in block 1 only and equals
+    -alpha H e^k_L, and C_alpha^{-1} of such a vector is computed mode by mode
+    with the recursion above."""
+    R = stability_function(z, Q)
+    return -alpha * R ** L / (1.0 - alpha * R ** L)

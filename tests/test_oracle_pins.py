@@ -1,0 +1,399 @@
+"""Pins of the CPU oracle against the paper, closed forms, textbook special
+cases, invariants and brute force (CPU only)."""
+import math
+
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+from conftest import read_golden
+from oracle import alpha_rule, collocation, fourier, operators, paradiag, sequential
+from paper_2103_12571_gb300 import workloads
+
+
+def small_prob(dim=1, nx=8, ny=4, nu=0.3, cx=0.0, cy=0.0, order=2, M=2, L=4, T=0.2):
+    return workloads.problem(dim, nx, ny, nu=nu, cx=cx, cy=cy, order=order, M=M, L=L, T=T)
+
+
+def setup(prob):
+    t = collocation.radau_iia_nodes(prob["M"])
+    Q = collocation.collocation_matrix(t)
+    A = operators.spatial_operator(prob)
+    return t, Q, A, prob["T"] / prob["L"]
+
+
+# ---------------------------------------------------------------- nodes / Q
+def test_nodes_match_printed_node_polynomials():
+    g = read_golden("radau_node_polynomials.txt")
+    for M, key in ((2, "w2"), (3, "w3")):
+        t = collocation.radau_iia_nodes(M)
+        np.testing.assert_allclose(np.poly(t), g[key], rtol=0, atol=1e-14)
+        assert t[-1] == 1.0
+    np.testing.assert_allclose(collocation.radau_iia_nodes(3)[:2],
+                               [(4 - math.sqrt(6)) / 10, (4 + math.sqrt(6)) / 10], atol=1e-15)
+    assert collocation.radau_iia_nodes(1).tolist() == [1.0]
+
+
+def test_Q_two_stage_is_textbook_radau_iia():
+    g = read_golden("radau_iia_m2_butcher.txt")
+    Q = collocation.collocation_matrix(collocation.radau_iia_nodes(2))
+    np.testing.assert_allclose(Q, [g["row1"], g["row2"]], atol=1e-15)
+
+
+def test_Q_three_stage_closed_form():
+    # exact entries of the three-stage Radau IIA matrix
+    s6 = math.sqrt(6)
+    ref = np.array([[(88 - 7 * s6) / 360, (296 - 169 * s6) / 1800, (-2 + 3 * s6) / 225],
+                    [(296 + 169 * s6) / 1800, (88 + 7 * s6) / 360, (-2 - 3 * s6) / 225],
+                    [(16 - s6) / 36, (16 + s6) / 36, 1 / 9]])
+    Q = collocation.collocation_matrix(collocation.radau_iia_nodes(3))
+    np.testing.assert_allclose(Q, ref, atol=2e-15)
+
+
+@pytest.mark.parametrize("M", [1, 2, 3, 4, 5])
+def test_Q_maps_monomials(M):
+    # eq. (vandermonde): Q W = D_M W, W_{mk} = t_m^k; last row = quadrature
+    # weights, exact for degree <= 2M - 2 (Radau)
+    t = collocation.radau_iia_nodes(M)
+    Q = collocation.collocation_matrix(t)
+    W = np.vander(t, M, increasing=True)
+    Wp = np.stack([t ** (k + 1) / (k + 1) for k in range(M)], axis=1)
+    np.testing.assert_allclose(Q @ W, Wp, atol=1e-13)
+    np.testing.assert_allclose(Q.sum(axis=1), t, atol=1e-14)
+    for k in range(2 * M - 1):
+        assert abs(Q[-1] @ t ** k - 1.0 / (k + 1)) < 1e-13
+
+
+# ------------------------------------------------------- Lemma 2 / eq. (QGL)
+def test_G_inverse_and_QH_identity():
+    for M in (2, 3):
+        t = collocation.radau_iia_nodes(M)
+        Q = collocation.collocation_matrix(t)
+        H = collocation.H_matrix(M)
+        for d in (-0.3 + 0.2j, 0.7, -1e-3j):
+            G = d * H + np.eye(M)
+            np.testing.assert_allclose(np.linalg.inv(G), np.eye(M) - d / (1 + d) * H, atol=1e-14)
+        np.testing.assert_allclose(Q @ H, np.diag(t) @ H, atol=1e-15)
+
+
+@pytest.mark.parametrize("M", [2, 3, 4])
+def test_lemma2_roots_are_eigenvalues(M):
+    t = collocation.radau_iia_nodes(M)
+    Q = collocation.collocation_matrix(t)
+    rng = np.random.default_rng(M)
+    for r in [0.0, 0.3, -0.2 + 0.1j] + list(rng.standard_normal(3) * 0.4 + 1j * rng.standard_normal(3) * 0.4):
+        B = Q - r * np.diag(t) @ collocation.H_matrix(M)
+        c = paradiag.lemma2_char_poly(t, r)
+        roots = np.sort_complex(np.roots(c[::-1]))
+        ev = np.sort_complex(np.linalg.eigvals(B))
+        np.testing.assert_allclose(roots, ev, atol=1e-11)
+
+
+def test_lemma2_printed_sign_is_the_other_shift():
+    # The lemma as printed (c_0 = (r+1) b_0, minus sign in c_m) gives the
+    # spectrum of Q + r D_t H_M, i.e. eq. (QGL) with r -> -r.
+    t = collocation.radau_iia_nodes(2)
+    Q = collocation.collocation_matrix(t)
+    r = 0.37
+    printed = paradiag.lemma2_char_poly(t, -r)
+    ev = np.sort_complex(np.linalg.eigvals(Q + r * np.diag(t) @ collocation.H_matrix(2)))
+    np.testing.assert_allclose(np.sort_complex(np.roots(printed[::-1])), ev, atol=1e-12)
+
+
+def test_M2_double_eigenvalue_where_discriminant_vanishes():
+    # p_2 = 2 l^2 + (2r - 4/3) l + (1 - r)/3 has discriminant
+    # proportional to 9 r^2 - 6 r - 2, zero at r = (1 +- sqrt 3)/3
+    t = collocation.radau_iia_nodes(2)
+    Q = collocation.collocation_matrix(t)
+    for r in ((1 + math.sqrt(3)) / 3, (1 - math.sqrt(3)) / 3):
+        c = paradiag.lemma2_char_poly(t, r)
+        np.testing.assert_allclose(c, [(1 - r) / 3, 2 * r - 4 / 3, 2], atol=1e-15)
+        ev = np.linalg.eigvals(Q - r * np.diag(t) @ collocation.H_matrix(2))
+        assert abs(ev[0] - ev[1]) < 1e-6
+    ev = np.linalg.eigvals(Q - 0.1 * np.diag(t) @ collocation.H_matrix(2))
+    assert abs(ev[0] - ev[1]) > 1e-2
+
+
+# ------------------------------------------------------------------ stencils
+@pytest.mark.parametrize("order", [2, 4])
+@pytest.mark.parametrize("dim", [1, 2])
+def test_stencil_symbol_is_eigenvalue(order, dim):
+    prob = small_prob(dim=dim, nx=16, ny=8, nu=0.7, cx=1.3, cy=-0.4, order=order)
+    A = operators.spatial_operator(prob)
+    sig = fourier.symbol(prob)
+    nx, ny = prob["nx"], prob["ny"]
+    for (kx, ky) in [(0, 0), (1, 0), (3, 2), (nx - 1, ny // 2)]:
+        if dim == 1:
+            e = np.exp(2j * np.pi * kx * np.arange(nx) / nx)
+            s = sig[kx]
+        else:
+            e = np.exp(2j * np.pi * (kx * np.arange(nx)[None, :] / nx + ky * np.arange(ny)[:, None] / ny)).reshape(-1)
+            s = sig[ky, kx]
+        np.testing.assert_allclose(A @ e, s * e, atol=1e-9 * max(1, abs(s)))
+
+
+def test_stencil_consistency_with_derivatives():
+    # order-p central differences of sin(2 pi x): error O(h^p)
+    for order in (2, 4):
+        errs = []
+        for n in (32, 64):
+            x = np.arange(n) / n
+            D1 = operators.first_derivative_1d(n, order=order)
+            D2 = operators.second_derivative_1d(n, order=order)
+            f = np.sin(2 * np.pi * x)
+            errs.append((np.max(np.abs(D1 @ f - 2 * np.pi * np.cos(2 * np.pi * x))),
+                         np.max(np.abs(D2 @ f + 4 * np.pi ** 2 * f))))
+        for i in range(2):
+            rate = math.log2(errs[0][i] / errs[1][i])
+            assert abs(rate - order) < 0.1
+
+
+# ------------------------------------------------------ sequential = C^{-1} w
+@pytest.mark.parametrize("M", [1, 2, 3])
+@pytest.mark.parametrize("dim", [1, 2])
+def test_sequential_equals_dense_allatonce_solve(M, dim):
+    prob = small_prob(dim=dim, nx=6, ny=4, nu=0.5, cx=0.8, cy=0.3, M=M, L=5, T=0.3)
+    t, Q, A, dT = setup(prob)
+    rng = np.random.default_rng(1)
+    N = operators.n_points(prob)
+    u0 = rng.standard_normal(N)
+    C = operators.allatonce_matrix(A, Q, dT, prob["L"]).toarray()
+    w = operators.rhs_w(u0, prob["L"], M)
+    dense = np.linalg.solve(C, w.reshape(-1)).reshape(w.shape)
+    seq = sequential.sequential_solve(A, Q, dT, prob["L"], u0)
+    np.testing.assert_allclose(seq, dense, atol=1e-13 * np.max(np.abs(dense)))
+    # apply_C block form equals the Kronecker matrix
+    np.testing.assert_allclose(operators.apply_C(seq, A, Q, dT).reshape(-1), C @ seq.reshape(-1), atol=1e-12)
+    assert np.max(np.abs(operators.residual(seq, u0, A, Q, dT))) < 1e-13
+
+
+def test_general_rhs_sweep_equals_dense():
+    prob = small_prob(dim=1, nx=8, M=3, L=4)
+    t, Q, A, dT = setup(prob)
+    rng = np.random.default_rng(2)
+    w = rng.standard_normal((4, 3, 8))
+    C = operators.allatonce_matrix(A, Q, dT, 4).toarray()
+    np.testing.assert_allclose(sequential.sequential_solve_general(A, Q, dT, w).reshape(-1),
+                               np.linalg.solve(C, w.reshape(-1)), atol=1e-13)
+
+
+def test_sequential_equals_fourier_closed_form_config1():
+    prob, u0, _ = workloads.config(1)
+    t, Q, A, dT = setup(prob)
+    seq = sequential.sequential_solve(A, Q, dT, prob["L"], u0)
+    modal = fourier.modal_solution(u0, prob, Q, dT, prob["L"])
+    np.testing.assert_allclose(seq, modal, atol=1e-14)
+
+
+def test_sequential_equals_fourier_closed_form_2d_advdiff():
+    prob = small_prob(dim=2, nx=16, ny=8, nu=0.01, cx=1.0, cy=0.5, M=3, L=8, T=0.1)
+    t, Q, A, dT = setup(prob)
+    u0 = workloads.random_phase_bumps_2d(16, 8, 3.0, seed=3)
+    seq = sequential.sequential_solve(A, Q, dT, prob["L"], u0)
+    modal = fourier.modal_solution(u0, prob, Q, dT, prob["L"])
+    np.testing.assert_allclose(seq, modal, atol=1e-13)
+    sel = fourier.modal_solution(u0, prob, Q, dT, prob["L"], blocks=[(7, 2), (3, 0)])
+    np.testing.assert_allclose(sel[(7, 2)], seq[7, 2], atol=1e-13)
+    np.testing.assert_allclose(sel[(3, 0)], seq[3, 0], atol=1e-13)
+
+
+# --------------------------------------------- stability function and order
+def test_stability_function_is_pade():
+    z = np.array([-0.3, -5.0 + 2j, 0.2j, -40.0, -1e-3])
+    Q2 = collocation.collocation_matrix(collocation.radau_iia_nodes(2))
+    Q3 = collocation.collocation_matrix(collocation.radau_iia_nodes(3))
+    R2 = (1 + z / 3) / (1 - 2 * z / 3 + z ** 2 / 6)
+    R3 = (1 + 2 * z / 5 + z ** 2 / 20) / (1 - 3 * z / 5 + 3 * z ** 2 / 20 - z ** 3 / 60)
+    np.testing.assert_allclose(fourier.stability_function(z, Q2), R2, rtol=1e-13)
+    np.testing.assert_allclose(fourier.stability_function(z, Q3), R3, rtol=1e-13)
+
+
+@pytest.mark.parametrize("M", [1, 2, 3])
+def test_convergence_order_2M_minus_1(M):
+    # one Fourier mode of the semi-discrete heat equation decays like
+    # exp(sigma t); the collocation error at T is O(dT^(2M-1))
+    prob = small_prob(dim=1, nx=16, nu=0.05, M=M, L=4, T=1.0)
+    k = 1
+    sig = fourier.symbol(prob)[k].real
+    Q = collocation.collocation_matrix(collocation.radau_iia_nodes(M))
+    errs = []
+    Ls = (4, 8, 16) if M < 3 else (2, 4, 8)
+    for L in Ls:
+        z = sig / L
+        errs.append(abs(fourier.stability_function(np.array([z]), Q)[0].real ** L - math.exp(sig)))
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
+    assert abs(rates[-1] - (2 * M - 1)) < 0.35, rates
+    # the same through the sequential solver on a grid mode
+    A = operators.spatial_operator(prob)
+    x = np.arange(16) / 16
+    u0 = np.cos(2 * np.pi * k * x)
+    uL = sequential.sequential_solve(A, Q, 1.0 / Ls[-1], Ls[-1], u0)[-1, -1]
+    assert np.max(np.abs(uL - math.exp(sig) * u0)) < 1.5 * errs[-1]
+
+
+# ------------------------------------------------------- Lemma 1 / C_alpha
+def test_lemma1_diagonalises_E_alpha():
+    for L, alpha in ((8, 1e-3), (5, 0.3), (16, 1e-6)):
+        V, Vinv, d = paradiag.lemma1(L, alpha)
+        E = operators.E_alpha(L, alpha).toarray()
+        # round-off scales with ||V|| ||V^{-1}|| <= L / alpha (proof of Theorem 2)
+        tol = 8 * L * 2.0 ** -52 * L / alpha
+        np.testing.assert_allclose(V @ np.diag(d) @ Vinv, E, atol=tol)
+        np.testing.assert_allclose(V @ Vinv, np.eye(L), atol=tol)
+        # time_forward / time_inverse are V^{-1}, V
+        rng = np.random.default_rng(L)
+        r = rng.standard_normal((L, 3))
+        np.testing.assert_allclose(paradiag.time_forward(r, alpha), Vinv @ r, atol=1e-12)
+        np.testing.assert_allclose(paradiag.time_inverse(r, alpha), V @ r, atol=tol)
+
+
+@pytest.mark.parametrize("dim,M", [(1, 2), (1, 3), (2, 3)])
+def test_precond_solve_inverts_C_alpha(dim, M):
+    prob = small_prob(dim=dim, nx=8, ny=4, nu=0.4, cx=0.7, cy=0.2, M=M, L=8, T=0.4)
+    t, Q, A, dT = setup(prob)
+    rng = np.random.default_rng(5)
+    N = operators.n_points(prob)
+    r = rng.standard_normal((8, M, N))
+    for alpha in (1e-2, 1e-5):
+        e = paradiag.precond_solve(A, Q, dT, alpha, r)
+        assert np.max(np.abs(e.imag)) < 1e-9
+        Ca = operators.allatonce_matrix(A, Q, dT, 8, alpha)
+        np.testing.assert_allclose(Ca @ e.real.reshape(-1), r.reshape(-1), atol=1e-10)
+
+
+# --------------------------------------------------- Richardson / Theorem 1
+def test_richardson_contraction_is_exact_per_mode():
+    prob = small_prob(dim=1, nx=8, nu=0.2, M=3, L=8, T=0.4)
+    t, Q, A, dT = setup(prob)
+    k = 2
+    x = np.arange(8) / 8
+    u0 = np.cos(2 * np.pi * k * x)
+    ustar = sequential.sequential_solve(A, Q, dT, 8, u0)
+    alpha = 0.05
+    its = paradiag.richardson(A, Q, dT, 8, u0, [alpha] * 4)
+    z = dT * fourier.symbol(prob)[k]
+    fac = fourier.contraction_factor(np.array([z]), alpha, 8, Q)[0].real
+    errs = [it[-1, -1] - ustar[-1, -1] for it in its]
+    for a, b in zip(errs[:-1], errs[1:]):
+        if np.max(np.abs(a)) > 1e-12:
+            np.testing.assert_allclose(b, fac * a, atol=1e-14 + 1e-9 * np.max(np.abs(a)))
+    assert abs(fac) <= alpha / (1 - alpha) + 1e-15
+    # mean mode: R = 1, factor is exactly -alpha / (1 - alpha) (Theorem 1 bound attained)
+    f0 = fourier.contraction_factor(np.array([0.0]), alpha, 8, Q)[0]
+    assert abs(f0 + alpha / (1 - alpha)) < 1e-15
+
+
+def test_richardson_forms_agree_and_converge():
+    prob = small_prob(dim=2, nx=4, ny=4, nu=0.3, cx=0.5, M=2, L=4, T=0.2)
+    t, Q, A, dT = setup(prob)
+    u0 = np.random.default_rng(7).standard_normal(16)
+    ustar = sequential.sequential_solve(A, Q, dT, 4, u0)
+    a = paradiag.richardson(A, Q, dT, 4, u0, [1e-3] * 6, form="paper")
+    b = paradiag.richardson(A, Q, dT, 4, u0, [1e-3] * 6, form="correction")
+    for x, y in zip(a, b):
+        np.testing.assert_allclose(x, y, atol=1e-12)
+    assert np.max(np.abs(a[-1] - ustar)) < 1e-13
+
+
+# --------------------------------------------------------------- Algorithm 2
+def test_alpha_sequence_reproduces_fig1():
+    g = read_golden("fig1_alpha_sequence.txt")
+    dT = g["T"][0] / g["L"][0]
+    m0 = g["m0_over_dT"][0] * dT
+    printed = g["alphas"]
+    # gamma is not printed; fit it to the first value, then the recursion
+    # must reproduce the other three to the printed digits
+    gam = printed[0] ** 2 * m0
+    alphas, ms = alpha_rule.alpha_sequence(m0, gam, kmax=4)
+    for a, p in zip(alphas, printed):
+        assert abs(a - p) / p < 0.5 * 10 ** -2 + 1e-3, (a, p)
+    for k in range(5):
+        assert abs(ms[k] - alpha_rule.m_closed_form(k, gam, m0)) <= 1e-12 * ms[k]
+    assert all(a <= 0.5 for a in alphas) and alphas == sorted(alphas)
+
+
+def test_alpha_sequence_limit():
+    alphas, ms = alpha_rule.alpha_sequence(1.0, 1e-10, kmax=60)
+    assert abs(ms[-1] - 4e-10) < 1e-15 and abs(alphas[-1] - 0.5) < 1e-9
+    assert alpha_rule.gamma(64, 2.0 ** -53, 0.0, 2.0) == 64 * 3 * 2.0 ** -53 * 2.0
+
+
+def test_algorithm2_driver_stops_on_last_block_difference():
+    prob = small_prob(dim=1, nx=8, nu=0.2, M=2, L=8, T=0.4)
+    t, Q, A, dT = setup(prob)
+    u0 = np.cos(2 * np.pi * np.arange(8) / 8)
+    w_inf = np.max(np.abs(u0))
+    gam = alpha_rule.gamma(8, 2.0 ** -53, 0.0, w_inf)
+
+    def iterate(u, m, alpha):
+        return paradiag.richardson(A, Q, dT, 8, u0, [alpha], u_init=u)[-1]
+
+    u_init = np.broadcast_to(u0, (8, 2, 8)).copy()
+    u, alphas, ms = alpha_rule.run_algorithm2(iterate, u_init, lambda v: v[-1], m0=dT * 8, gam=gam, tol=1e-12)
+    ustar = sequential.sequential_solve(A, Q, dT, 8, u0)
+    assert np.max(np.abs(u - ustar)) < 1e-11
+    assert len(alphas) <= 6
+
+
+# ------------------------------------------------------------------- adjoint
+def test_apply_CT_is_transpose():
+    prob = small_prob(dim=2, nx=4, ny=4, nu=0.3, cx=0.9, cy=-0.6, M=3, L=4, T=0.2)
+    t, Q, A, dT = setup(prob)
+    C = operators.allatonce_matrix(A, Q, dT, 4).toarray()
+    lam = np.random.default_rng(3).standard_normal((4, 3, 16))
+    np.testing.assert_allclose(operators.apply_CT(lam, A, Q, dT).reshape(-1), C.T @ lam.reshape(-1), atol=1e-12)
+
+
+def test_sequential_adjoint_dot_product():
+    prob = small_prob(dim=2, nx=8, ny=4, nu=0.3, cx=0.9, cy=-0.6, M=3, L=6, T=0.3)
+    t, Q, A, dT = setup(prob)
+    rng = np.random.default_rng(4)
+    w = rng.standard_normal((6, 3, 32))
+    g = rng.standard_normal((6, 3, 32))
+    u = sequential.sequential_solve_general(A, Q, dT, w)
+    lam = sequential.sequential_adjoint(A, Q, dT, g)
+    assert abs(np.sum(u * g) - np.sum(w * lam)) < 1e-12 * np.sum(np.abs(u * g))
+    C = operators.allatonce_matrix(A, Q, dT, 6).toarray()
+    np.testing.assert_allclose(C.T @ lam.reshape(-1), g.reshape(-1), atol=1e-12)
+
+
+def test_gradients_match_central_differences():
+    base = small_prob(dim=2, nx=8, ny=8, nu=0.05, cx=1.0, cy=0.5, M=3, L=4, T=0.1)
+    u0 = workloads.smoothed_noise_2d(8, 8, 1.0, seed=0)
+    target = workloads.smoothed_noise_2d(8, 8, 1.0, seed=1)
+    Q = collocation.collocation_matrix(collocation.radau_iia_nodes(3))
+    dT = base["T"] / base["L"]
+
+    def loss(p, v0):
+        A = operators.spatial_operator(p)
+        uL = sequential.sequential_solve(A, Q, dT, p["L"], v0)[-1, -1]
+        return np.sum((uL - target) ** 2)
+
+    A = operators.spatial_operator(base)
+    u = sequential.sequential_solve(A, Q, dT, base["L"], u0)
+    g = np.zeros_like(u)
+    g[-1, -1] = 2 * (u[-1, -1] - target)
+    lam = sequential.sequential_adjoint(A, Q, dT, g)
+    du0, dnu, dc = sequential.grad_params(base, Q, dT, u, lam)
+    h = 1e-6
+    for key, val in (("nu", dnu), ("cx", dc[0]), ("cy", dc[1])):
+        pp, pm = dict(base), dict(base)
+        pp[key] += h
+        pm[key] -= h
+        fd = (loss(pp, u0) - loss(pm, u0)) / (2 * h)
+        assert abs(fd - val) <= 1e-7 * max(1.0, abs(val)), (key, fd, val)
+    rng = np.random.default_rng(9)
+    for _ in range(3):
+        v = rng.standard_normal(64)
+        fd = (loss(base, u0 + h * v) - loss(base, u0 - h * v)) / (2 * h)
+        assert abs(fd - du0 @ v) <= 1e-7 * max(1.0, abs(fd))
+
+
+def test_workloads_deterministic_and_shaped():
+    for i in (1, 3, 4):
+        p, u0, ex = workloads.config(i)
+        p2, u02, _ = workloads.config(i)
+        assert u0.shape == (operators.n_points(p),)
+        np.testing.assert_array_equal(u0, u02)
+    u = workloads.random_phase_bumps_2d(32, 32, 4.0, seed=1)
+    assert abs(np.max(np.abs(u)) - 1) < 1e-15
