@@ -1,0 +1,335 @@
+"""Benchmark of the alpha-circulant preconditioned Richardson iteration on
+one GB300 (or N independent replicas, one per GPU under torchrun).
+
+Workload: 2D heat u_t = 0.05 Lap u on the periodic unit square, 256 x 256
+grid, 5-point Laplacian, Radau IIA with M = 3 nodes, L = 64 time steps,
+T = 0.5, u0 a seeded sum of 16 Fourier modes (|k| <= 8) -- the paper's
+periodic heat test shape with synthetic data.  One step = one Richardson
+iteration u <- u + C_alpha^{-1}(w - C u) of the mixed form (FP64 residual and
+update, complex64 preconditioner) with the mixed-rule alpha.
+
+Prints one JSON line (rank 0).  --impl reference times the CPU oracle
+instead.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+CONFIG = 2
+TOL = 1e-10
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def flush_l2(torch, buf):
+    buf.add_(1.0)
+
+
+def fp64_flops_per_dof(M, taps):
+    # residual of one DoF: stencil (1 mul + taps-1 fma), M fma of the node
+    # mix, 1 fma of the coupling term, plus 1/M mul for s_l * u_{l-1,M};
+    # flops count an fma as 2
+    return (1 + 2 * (taps - 1)) + 2 * M + 2 + 1.0 / M
+
+
+def run_ours(args):
+    import torch
+    from paper_2103_12571_gb300 import workloads
+    from paper_2103_12571_gb300.api import Plan
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    prob, u0_np, ex = workloads.config(CONFIG)
+    L, M = prob["L"], prob["M"]
+    N = prob["nx"] * prob["ny"]
+    D = L * M * N
+    plan = Plan(prob, precision="c64", alpha="mixed", max_iter=60)
+    u0 = torch.from_numpy(u0_np).cuda()
+    alpha = min(0.25, max(1e-8, (L * 3 * 2.0 ** -24) ** 0.5))
+    u = u0.repeat(L * M).reshape(L, M, N).contiguous()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    st = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        plan.richardson_step(alpha, u0, u)
+    torch.cuda.synchronize()
+
+    # ---- device-timed steps (inputs resident in HBM), L2 flushed between steps
+    plan.profile(True)
+    launches0 = plan.info()["launches"]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        flush_l2(torch, flush)
+        ev[i][0].record(st)
+        plan.richardson_step(alpha, u0, u)
+        ev[i][1].record(st)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    launches = plan.info()["launches"] - launches0
+    prof = plan.profile_read()
+    plan.profile(False)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms = float(np.mean(step_ms))
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = D * world / (ms * 1e-3)
+
+    # ---- end to end through the public API: pinned host u0 -> device, one
+    # iteration with its residual norm read back to the host
+    u0_host = torch.from_numpy(u0_np).pin_memory()
+    u0_dev = torch.empty_like(u0)
+    for _ in range(2):
+        u0_dev.copy_(u0_host, non_blocking=True)
+        plan.richardson_step(alpha, u0_dev, u, want_residual=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        u0_dev.copy_(u0_host, non_blocking=True)
+        plan.richardson_step(alpha, u0_dev, u, want_residual=True)
+    torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+    grid = plan.info()["N"] // plan.info()["tile_fwd"]
+
+    # ---- time to a 1e-10 relative residual: FP64 (Algorithm 2) vs mixed
+    ttt = {}
+    for name, prec, mode in (("fp64", "c128", "paper"), ("mixed", "c64", "mixed")):
+        p2 = plan if prec == "c64" else Plan(prob, precision=prec, alpha=mode, max_iter=60)
+        p2.solve(u0, TOL)  # warm
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        uu, stt = p2.solve(u0, TOL)
+        b.record(st)
+        torch.cuda.synchronize()
+        ttt[name] = {"ms": round(a.elapsed_time(b), 3), "iters": stt["iters"],
+                     "res_rel": stt["res_rel"][-1]}
+        if prec == "c128":
+            p2.profile(True)
+            p2.richardson_step(1e-6, u0, uu)
+            ttt[name]["kernel_ms"] = {k: round(v[0], 4) for k, v in p2.profile_read().items() if v[1]}
+            del p2
+
+    # ---- roofline of the dominant kernel
+    kern = {k: v for k, v in prof.items() if v[1] > 0}
+    total_ms = sum(v[0] for v in kern.values())
+    dom = max(kern, key=lambda k: kern[k][0])
+    dom_ms = kern[dom][0] / kern[dom][1]
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    fp64_peak = 2 * 2 * 152 * 2.07e9 / 1e12  # 2 DFMA/clk/SM x 152 SMs x 2.07 GHz x 2 flop
+    csz = 8
+    F = L // 2 + 1
+    if dom == "resid_tfft_mix":
+        flops = fp64_flops_per_dof(M, 5) * D
+        roof = {"bound": "alu", "achieved": flops / (dom_ms * 1e-3) / 1e12, "peak": fp64_peak,
+                "unit": "TFLOP/s", "peak_kind": "FP64 FMA pipe, 2/clk/SM at 2.07 GHz (derived)"}
+        roof["frac"] = roof["achieved"] / roof["peak"]
+        roof["hbm_gbs_algorithmic"] = (8.0 * D + F * M * N * csz) / (dom_ms * 1e-3) / 1e9
+    else:
+        bytes_ = {"spatial_solve": 6 * F * M * N * csz,
+                  "mix_tifft_update": F * M * N * csz + 16.0 * D}.get(dom, 16.0 * D)
+        roof = {"bound": "hbm", "achieved": bytes_ / (dom_ms * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s"}
+        roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["kernel"] = dom
+    roof["kernel_ms"] = dom_ms
+    roof["traffic"] = None
+    out = {
+        "metric": "space-time DoF*iterations/s (one alpha-circulant Richardson iteration, mixed FP64/c64)",
+        "value": value, "unit": "DoF*it/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64+c64", "data": "synthetic",
+        "config": {"workload": ex["name"], "N": N, "M": M, "L": L, "T": prob["T"], "DoF": D,
+                   "precision": "fp64 residual/update + complex64 preconditioner", "alpha": alpha,
+                   "l2": "flushed between timed steps (256 MB write)", "parallelism": "replicas" if world > 1 else "1 GPU"},
+        "e2e": {"value": D / (e2e_ms * 1e-3) * world, "unit": "DoF*it/s", "ms_per_step": e2e_ms,
+                "h2d_bytes_per_step": N * 8, "d2h_bytes_per_step": grid * 4},
+        "gpu_launches": int(launches),
+        "kernels_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in kern.items()},
+        "time_to_1e-10": ttt,
+        "roofline": roof,
+        "clocks": clk,
+        "wall_s_timed": wall,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(prob, u0_np, samples=args.cpu_samples)
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def oracle_iteration_sample(prob, u0, nblocks, alpha=3e-3):
+    """Time the oracle's Richardson iteration on a bounded sample: the full
+    FP64 residual and time transforms, and `nblocks` of the L per-frequency
+    block solves (sparse LU), scaled to a whole iteration."""
+    import scipy.sparse.linalg as spla
+    from oracle import collocation, operators, paradiag
+
+    t = collocation.radau_iia_nodes(prob["M"])
+    Q = collocation.collocation_matrix(t)
+    A = operators.spatial_operator(prob)
+    L, M = prob["L"], prob["M"]
+    dT = prob["T"] / L
+    N = A.shape[0]
+    u = np.broadcast_to(u0, (L, M, N)).copy()
+    t0 = time.perf_counter()
+    r = operators.residual(u, u0, A, Q, dT)
+    x = paradiag.time_forward(r.astype(np.complex128), alpha)
+    d = paradiag.eigenvalues_d(L, alpha)
+    t1 = time.perf_counter()
+    ts = []
+    for l in range(nblocks):
+        a = time.perf_counter()
+        lu = spla.splu(paradiag.block_matrix(A, Q, dT, d[l]).astype(np.complex128))
+        x[l] = lu.solve(x[l].reshape(-1)).reshape(M, N)
+        ts.append(time.perf_counter() - a)
+    t2 = time.perf_counter()
+    e = paradiag.time_inverse(x, alpha)
+    u += e.real
+    t3 = time.perf_counter()
+    per_iter = (t1 - t0) + (t3 - t2) + np.mean(ts) * L
+    return per_iter, (t3 - t0)
+
+
+def cpu_baseline(prob, u0, samples=2):
+    threads = os.environ.get("OMP_NUM_THREADS") or str(os.cpu_count())
+    per_iter, spent = oracle_iteration_sample(prob, u0, samples)
+    D = prob["L"] * prob["M"] * prob["nx"] * prob["ny"]
+    return {"value": D / per_iter, "unit": "DoF*it/s", "cores": int(threads) if threads.isdigit() else os.cpu_count(),
+            "kind": "oracle",
+            "sample": "one oracle Richardson iteration (FP64 residual, numpy time FFTs, %d of %d per-frequency "
+                      "sparse-LU block solves, scaled to all %d); %.1f s of CPU time" % (samples, prob["L"], prob["L"], spent),
+            "cpu": os.cpu_count()}
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    from paper_2103_12571_gb300 import workloads
+    prob, u0, ex = workloads.config(CONFIG)
+    D = prob["L"] * prob["M"] * prob["nx"] * prob["ny"]
+    for _ in range(args.warmup):
+        oracle_iteration_sample(prob, u0, 1)
+    per = []
+    spent = 0.0
+    for _ in range(args.steps):
+        p, s = oracle_iteration_sample(prob, u0, 1)
+        per.append(p)
+        spent += s
+    ms = float(np.mean(per)) * 1e3
+    value = D / (ms * 1e-3)
+    cores = os.cpu_count()
+    out = {"impl": "reference",
+           "metric": "space-time DoF*iterations/s (one alpha-circulant Richardson iteration, mixed FP64/c64)",
+           "value": value, "unit": "DoF*it/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": ex["name"], "DoF": D},
+           "cpu_baseline": {"value": value, "unit": "DoF*it/s", "cores": cores, "kind": "oracle",
+                            "sample": "per step: one oracle Richardson iteration with 1 of %d per-frequency "
+                                      "sparse-LU block solves timed and scaled; %.1f s total" % (prob["L"], spent)},
+           "e2e": {"value": value, "unit": "DoF*it/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-samples", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

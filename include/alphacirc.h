@@ -1,0 +1,226 @@
+/*
+ * alphacirc.h — C ABI of the GB300 alpha-circulant preconditioned Richardson
+ * solver for the all-at-once Radau IIA collocation system of a linear,
+ * periodic, constant-coefficient PDE  u_t = A u  (+ an optional right-hand side).
+ *
+ * Method: Caklovic, Speck & Frank, "A parallel-in-time collocation method using
+ * diagonalization: theory and implementation for linear problems"
+ * (arXiv 2103.12571).  Equation, lemma and algorithm numbers below refer to it.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Layout of every space-time vector: u[l][m][n], double, l = 0..L-1 (time
+ *   step), m = 0..M-1 (collocation node), n = 0..N-1 (grid point), n fastest;
+ *   in 2D n = iy * nx + ix.  This is the ordering of eq. (globalsys).
+ * - "device" pointers are CUDA global-memory pointers on the device that was
+ *   current at ac_setup(); "host" pointers are ordinary CPU memory.  The
+ *   caller owns every pointer it passes; the plan owns its own workspace.
+ * - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *   Every call is ordered on that stream.  Only ac_richardson_solve and
+ *   ac_adjoint_solve synchronise the host (once per iteration, to read a few
+ *   scalars); ac_grad_params synchronises once.
+ * - Return value: AC_OK (0) or a negative AC_ERR_* code.  No exception ever
+ *   crosses this boundary.  ac_status_string() names a code; ac_last_error()
+ *   returns a thread-local message with detail about the last failure.
+ * - Device work runs only in this library's own CUDA kernels: there is no
+ *   CPU fallback.  A call that cannot run on the GPU returns an error.
+ */
+#ifndef ALPHACIRC_H
+#define ALPHACIRC_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define AC_OK                      0
+#define AC_ERR_INVALID_ARG        -1  /* bad size, null pointer, unsupported combination   */
+#define AC_ERR_NOT_DIAGONALIZABLE -2  /* Q G_l^{-1} numerically defective (Lemma 2, Sec. 2.3) */
+#define AC_ERR_NO_CONVERGENCE     -3  /* max_iter reached, or the residual grew 3 times      */
+#define AC_ERR_INNER_BREAKDOWN    -4  /* BiCGStab breakdown / iteration cap in an inner solve */
+#define AC_ERR_CUDA               -5  /* a CUDA runtime call failed (see ac_last_error)      */
+#define AC_ERR_NOT_FINITE         -6  /* NaN or Inf met in a residual norm                   */
+
+/* ---- option values ------------------------------------------------------ */
+#define AC_C128 0   /* preconditioner (steps ii-iv) in complex128                     */
+#define AC_C64  1   /* preconditioner in complex64; residual and update stay FP64    */
+
+#define AC_INNER_FFT      0  /* exact spatial-FFT solve of eq. (d2)                    */
+#define AC_INNER_BICGSTAB 1  /* batched BiCGStab on the stencil, relative tolerance tau */
+
+#define AC_ALPHA_FIXED 0  /* alpha_k = alpha0 for every k                                 */
+#define AC_ALPHA_PAPER 1  /* Algorithm 2: alpha_{k+1} = sqrt(gamma/m_k), m_{k+1} = 2 sqrt(m_k gamma) */
+#define AC_ALPHA_MIXED 2  /* fixed alpha = sqrt(L (3 eps_p + tau)), clamped to [1e-8, 0.25] */
+
+#define AC_STOP_RESIDUAL 0  /* ||w - C u||_2 <= tol ||w||_2                               */
+#define AC_STOP_PAPER    1  /* Algorithm 2: m_k <= tol, or ||u_L^{k+1} - u_L^k||_inf <= tol */
+
+#define AC_MAX_STATS 128
+
+/* Spatial operator A = nu * Lap_h - cx * D_x - cy * D_y on the periodic box
+ * [0,lx) x [0,ly) with nx (x ny) points, central differences of order 2 or 4
+ * (Sec. 5 uses periodic central/upwind stencils; the standard central
+ * coefficients are used here).  dim = 1 ignores ny, ly, cy. */
+typedef struct {
+    int dim;          /* 1 or 2                                     */
+    int nx, ny;       /* grid points per axis (powers of two for AC_INNER_FFT) */
+    double lx, ly;    /* box lengths                                */
+    double nu;        /* diffusion coefficient                      */
+    double cx, cy;    /* advection velocity                         */
+    int order;        /* 2 or 4                                     */
+} ac_problem;
+
+/* Choice of alpha_k per iteration (Sec. 3.3). */
+typedef struct {
+    int mode;         /* AC_ALPHA_FIXED | AC_ALPHA_PAPER | AC_ALPHA_MIXED            */
+    double alpha0;    /* FIXED: the alpha; others: ignored                            */
+    double m0;        /* PAPER: estimate of ||u^(0) - u*||_inf; <= 0 selects the
+                         bound T (||A||_inf max|u0|) of Sec. 3.3                      */
+    double tau;       /* inner-solve relative tolerance (BiCGStab), used in gamma too */
+    int max_iter;     /* outer iteration cap (<= AC_MAX_STATS)                        */
+    int stop_rule;    /* AC_STOP_RESIDUAL | AC_STOP_PAPER                             */
+} ac_alpha_schedule;
+
+/* Per-solve record (host memory, filled by the solve calls). */
+typedef struct {
+    int iters;                        /* outer iterations performed                    */
+    int converged;                    /* 1 if the stop rule was met                     */
+    double res_rel[AC_MAX_STATS];     /* ||w - C u^(k)||_2 / ||w||_2, k = 0..iters      */
+    double alpha[AC_MAX_STATS];       /* alpha_{k+1} used in iteration k                */
+    double m[AC_MAX_STATS];           /* Algorithm 2's m_k (0 for other modes)          */
+    double diff_last[AC_MAX_STATS];   /* ||u_L^{(k+1)} - u_L^{(k)}||_inf                 */
+    int inner_iters[AC_MAX_STATS];    /* BiCGStab: max iterations over systems, per k   */
+    double w_norm2;                   /* ||w||_2                                         */
+    double w_inf;                     /* ||w||_inf                                       */
+} ac_stats;
+
+/* Shape and tuning facts of a plan. */
+typedef struct {
+    int N, M, L, F;                   /* F = L/2 + 1 stored time frequencies            */
+    int tile_fwd, tile_upd;           /* grid points per CTA in the time kernels        */
+    int spatial_path;                 /* 0: 1D one CTA per plane, 1: 2D one CTA per plane, 2: 2D three passes, 3: BiCGStab */
+    long long workspace_bytes;        /* device memory owned by the plan               */
+    long long launches;               /* kernels launched by this plan so far          */
+} ac_plan_info;
+
+typedef struct ac_plan ac_plan;
+
+/* ---- plan ---------------------------------------------------------------- */
+
+/* Builds the host tables (Radau IIA nodes and Q of eq. (collocation), stencil
+ * coefficients and symbols, FFT twiddles) and allocates the device workspace
+ * (F*M*N complex plus small tables) on the current CUDA device.
+ * M >= 1 (<= 4), L a power of two (2..1024), dT > 0.  Writes *out.
+ * Errors: AC_ERR_INVALID_ARG for unsupported sizes, AC_ERR_CUDA. */
+int ac_setup(const ac_problem* prob, int M, int L, double dT,
+             const ac_alpha_schedule* sched, int precision, int inner,
+             ac_plan** out);
+
+/* Frees the plan and its device memory.  NULL is ignored. */
+void ac_destroy(ac_plan* plan);
+
+int ac_plan_get_info(const ac_plan* plan, ac_plan_info* info);
+
+/* ---- operators (eq. (globalsys)) ---------------------------------------- */
+
+/* Cu = C u with C = I_L (x) C_coll + E (x) H, C_coll = I - dT Q (x) A, in FP64.
+ * u, Cu: device, L*M*N doubles, must not overlap. */
+int ac_apply_C(ac_plan* plan, const double* u, double* Cu, void* stream);
+
+/* out = C^T lam (FP64).  lam, out: device, L*M*N doubles. */
+int ac_apply_CT(ac_plan* plan, const double* lam, double* out, void* stream);
+
+/* ---- one preconditioner solve (Lemma 1, eqs. (s1)-(s3), Algorithm 1) ---- */
+
+/* e = C_alpha^{-1} r with C_alpha = I_L (x) C_coll + E_alpha (x) H (eq. (prec)):
+ * alpha-scaling along time, length-L FFT (eq. (s1)), node mixing with the
+ * eigenbasis of Q G_l^{-1} (eq. (d1)), the shifted spatial solves of eq. (d2),
+ * back-mixing with G_l^{-1} S_l (eqs. (d3), (Gsubstitution)), inverse FFT and
+ * un-scaling (eq. (s3)).  0 < alpha < 1.  r, e: device, L*M*N doubles; r and e
+ * may be the same buffer.  Runs in the plan's precision. */
+int ac_precond_solve(ac_plan* plan, double alpha, const double* r, double* e,
+                     void* stream);
+
+/* ---- Richardson iteration (eq. (Riteration), correction form) ----------- */
+
+/* One iteration u <- u + C_alpha^{-1} (w - C u) with w = (u0 stacked over the
+ * M nodes in block 1) + b.  u0: device, N doubles (may be NULL = 0); b: device,
+ * L*M*N doubles or NULL; u: device, in/out.  If res_rel_out is not NULL the
+ * call synchronises and stores ||w - C u_in||_2 / ||w||_2 there (with
+ * ||w||_2 as computed at this call).  No host synchronisation otherwise. */
+int ac_richardson_step(ac_plan* plan, double alpha, const double* u0,
+                       const double* b, double* u, double* res_rel_out,
+                       void* stream);
+
+/* Full solve of C u = w by Richardson iterations with the plan's alpha
+ * schedule (Algorithm 1 with Algorithm 2 or a fixed/mixed rule) and stop
+ * rule; stops after at most sched.max_iter iterations.  If init_u is nonzero,
+ * u holds the initial iterate on entry, else u^(0) = (u0, ..., u0) (Sec. 5).
+ * tol: the stop tolerance of the plan's stop rule.  stats: host, may be NULL.
+ * Returns AC_ERR_NO_CONVERGENCE if the rule was not met (u then holds the
+ * last iterate). */
+int ac_richardson_solve(ac_plan* plan, const double* u0, const double* b,
+                        double* u, int init_u, double tol, ac_stats* stats,
+                        void* stream);
+
+/* ---- adjoint (not in the paper; derived from eq. (globalsys)) ----------- */
+
+/* lam = C^{-T} g.  Reversing the time index turns C^T into a system of the
+ * same all-at-once form with Q -> Q^T, A -> A^T and H_M -> H_M^T, which the
+ * same alpha-circulant kernels solve.  g, lam: device, L*M*N doubles, distinct.
+ * lam^(0) = 0.  Same schedule and stop rule as the forward solve, with g in
+ * the role of w. */
+int ac_adjoint_solve(ac_plan* plan, const double* g, double* lam, double tol,
+                     ac_stats* stats, void* stream);
+
+/* Gradient contractions for a loss J(u) with C(theta) u = w(u0) and
+ * lam = C^{-T} dJ/du:
+ *   du0[n]        = sum_m lam[0][m][n]                         (device, N doubles)
+ *   dparams[0]    = dJ/dnu = dT sum_l sum_{m,j} Q_mj lam_{l,m} . Lap u_{l,j}
+ *   dparams[1..2] = dJ/dcx, dJ/dcy = -dT sum ... lam . D_{x,y} u     (host, 3 doubles)
+ * u, lam: device, L*M*N doubles.  du0 may be NULL.  Synchronises once. */
+int ac_grad_params(ac_plan* plan, const double* u, const double* lam,
+                   double* du0, double* dparams, void* stream);
+
+/* ---- host-side planner (no GPU needed) ---------------------------------- */
+
+/* Radau IIA nodes 0 < t_1 < ... < t_M = 1 (roots of P_{M-1} + P_M mapped by
+ * x = 1 - 2t, Sec. 2.3).  t: host, M doubles.  1 <= M <= 8. */
+int ac_radau_nodes(int M, double* t);
+
+/* Collocation matrix q_{mi} = int_0^{t_m} c_i(s) ds of eq. (collocation).
+ * Q: host, M*M doubles, row-major. */
+int ac_collocation_matrix(int M, double* Q);
+
+/* Per-frequency tables used by the kernels for a given alpha (Lemma 1 and
+ * eqs. (QGL), (d1)-(d3), Algorithm 1): for f = 0..L/2,
+ *   d_f = -alpha^{1/L} exp(-2 pi i f / L),  G_f = I + d_f H_M  (H_M^T if transposed),
+ *   B_f = Q G_f^{-1} (Q^T G_f^{-1} if transposed) = S_f diag(mu_f) S_f^{-1},
+ *   Sinv_f = S_f^{-1},  P_f = G_f^{-1} S_f.
+ * Outputs (host, interleaved re/im doubles): mu [F][M][2], Sinv [F][M][M][2],
+ * P [F][M][M][2]; cond: host, F doubles (condition number of S_f), may be NULL.
+ * Returns AC_ERR_NOT_DIAGONALIZABLE if some cond(S_f) > 1e10. */
+int ac_freq_tables(int M, int L, double alpha, int transposed,
+                   double* mu, double* Sinv, double* P, double* cond);
+
+/* Algorithm 2's sequence: alphas[k] = alpha_{k+1}, ms[k] = m_k (ms[0] = m0),
+ * k = 0..n-1 (ms has n+1 entries). */
+int ac_alpha_sequence(double m0, double gamma, int n, double* alphas, double* ms);
+
+/* ---- instrumentation ---------------------------------------------------- */
+
+/* Per-kernel CUDA-event timing inside the library (on the stream each kernel
+ * is launched on).  on = 1 enables and zeroes the accumulators. */
+int ac_profile_enable(ac_plan* plan, int on);
+/* names: up to `cap` kernels; for each: accumulated milliseconds, launch count.
+ * Synchronises the device.  Returns the number of kernel kinds. */
+int ac_profile_read(ac_plan* plan, int cap, const char** names, double* ms,
+                    long long* count);
+
+const char* ac_status_string(int status);
+const char* ac_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ALPHACIRC_H */

@@ -1,0 +1,843 @@
+// C ABI of the alpha-circulant Richardson solver: plan set-up, table
+// management and the launch sequences of Algorithm 1 (one iteration), the
+// Richardson loop with the alpha rules of Sec. 3.3 / Algorithm 2, the adjoint
+// solve and the gradient contractions.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "alphacirc.h"
+#include "kernels.h"
+#include "planner.h"
+
+namespace ac {
+cudaError_t launch_wnorms(const double* u0, const double* b, int L, int M, long long N, double* part,
+                          int grid, cudaStream_t st);
+cudaError_t launch_fill_stack(const double* u0, double* u, int L, int M, long long N, cudaStream_t st);
+}
+
+using ac::cd;
+
+static thread_local std::string g_err;
+
+static int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define CK(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return fail(AC_ERR_CUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_),  \
+                        __FILE__, __LINE__);                                                  \
+    } while (0)
+
+enum KernelKind { KK_FWD = 0, KK_SPACE, KK_UPD, KK_APPLY, KK_GRAD, KK_AUX, KK_COUNT };
+static const char* kKindNames[KK_COUNT] = {"resid_tfft_mix", "spatial_solve", "mix_tifft_update",
+                                           "apply_C", "grad_contract", "aux"};
+
+struct EventPair {
+    int kind;
+    cudaEvent_t a, b;
+};
+
+struct ac_plan {
+    ac_problem prob;
+    int M, L, logL, F, N, P, grid;
+    double dT;
+    ac_alpha_schedule sched;
+    int precision, inner, device;
+    int spatial_path;
+    int rows_per_block, cols_per_block;
+    size_t csize;  // bytes per complex of the transform type
+    // host data
+    double t[8], Q[64];
+    ac::Grid grid_fwd, grid_adj;  // A and A^T
+    double d1x[5], d2x[5], d1y[5], d2y[5];
+    // device buffers
+    void* X = nullptr;
+    void* tw_L = nullptr;
+    void* tw_x = nullptr;
+    void* tw_y = nullptr;
+    void* sig_x = nullptr;   // A
+    void* sig_y = nullptr;
+    void* sigT_x = nullptr;  // A^T
+    void* sigT_y = nullptr;
+    double* d_qs = nullptr;
+    double* d_s = nullptr;
+    float* d_inv_s_w = nullptr;
+    double* d_sinv = nullptr;
+    void* d_Sinv = nullptr;
+    void* d_P = nullptr;
+    void* d_mu = nullptr;
+    float* d_part_fwd = nullptr;
+    float* d_part_upd = nullptr;
+    double* d_part_d = nullptr;  // FP64 reductions
+    double* d_dtQ = nullptr;     // dT Q
+    double* d_dtQT = nullptr;    // dT Q^T
+    float* h_part_fwd = nullptr;  // pinned
+    float* h_part_upd = nullptr;
+    double* h_part_d = nullptr;
+    int part_d_len = 0;
+    // table cache key
+    double cur_alpha = -1.0;
+    int cur_transposed = -1;
+    double cur_wscale = -1.0;
+    long long workspace = 0;
+    long long launches = 0;
+    cudaEvent_t ev_res = nullptr;
+    // profiling
+    bool prof = false;
+    std::vector<EventPair> pending;
+    std::vector<cudaEvent_t> pool;
+    double prof_ms[KK_COUNT] = {0};
+    long long prof_count[KK_COUNT] = {0};
+};
+
+// ----------------------------------------------------------------- helpers
+static cudaEvent_t get_event(ac_plan* p) {
+    if (!p->pool.empty()) {
+        cudaEvent_t e = p->pool.back();
+        p->pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+struct ProfScope {
+    ac_plan* p;
+    int kind;
+    cudaStream_t st;
+    cudaEvent_t a = nullptr;
+    ProfScope(ac_plan* p_, int k, cudaStream_t s) : p(p_), kind(k), st(s) {
+        if (p->prof) {
+            a = get_event(p);
+            cudaEventRecord(a, st);
+        }
+    }
+    ~ProfScope() {
+        if (p->prof && a) {
+            cudaEvent_t b = get_event(p);
+            cudaEventRecord(b, st);
+            p->pending.push_back({kind, a, b});
+        }
+    }
+};
+
+static void drain_profile(ac_plan* p) {
+    for (auto& e : p->pending) {
+        cudaEventSynchronize(e.b);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e.a, e.b);
+        p->prof_ms[e.kind] += ms;
+        p->prof_count[e.kind] += 1;
+        p->pool.push_back(e.a);
+        p->pool.push_back(e.b);
+    }
+    p->pending.clear();
+}
+
+template <typename T>
+static cudaError_t dalloc(ac_plan* p, T** ptr, size_t bytes) {
+    p->workspace += (long long)bytes;
+    return cudaMalloc((void**)ptr, bytes);
+}
+
+static int ilog2(int v) {
+    int l = 0;
+    while ((1 << l) < v) ++l;
+    return l;
+}
+static bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+// Upload a complex table in the transform precision.
+static cudaError_t upload_c(const ac_plan* p, void* dst, const cd* src, size_t n, cudaStream_t st) {
+    if (p->precision == AC_C128) {
+        return cudaMemcpyAsync(dst, src, n * sizeof(cd), cudaMemcpyHostToDevice, st);
+    }
+    std::vector<float> tmp(2 * n);
+    for (size_t i = 0; i < n; ++i) {
+        tmp[2 * i] = (float)src[i].real();
+        tmp[2 * i + 1] = (float)src[i].imag();
+    }
+    return cudaMemcpyAsync(dst, tmp.data(), tmp.size() * sizeof(float), cudaMemcpyHostToDevice, st);
+}
+
+static void twiddles(int n, std::vector<cd>& tw) {
+    tw.resize(std::max(1, n / 2));
+    for (int k = 0; k < n / 2; ++k) tw[k] = std::exp(cd(0.0, -2.0 * M_PI * k / n));
+    if (n / 2 == 0) tw[0] = 1.0;
+}
+
+// Alpha-dependent tables: qs, s, inv_s_w, sinv (FP64/FP32) and the per-frequency
+// Sinv, P, dT mu (transform precision).
+static int ensure_tables(ac_plan* p, double alpha, int transposed, double wscale, cudaStream_t st) {
+    if (alpha == p->cur_alpha && transposed == p->cur_transposed && wscale == p->cur_wscale) return AC_OK;
+    if (!(alpha > 0.0) || !(alpha < 1.0)) return fail(AC_ERR_INVALID_ARG, "alpha must be in (0,1), got %g", alpha);
+    const int L = p->L, M = p->M, F = p->F;
+    std::vector<double> qs((size_t)L * M * M), s(L), sinv(L);
+    std::vector<float> isw(L);
+    for (int l = 0; l < L; ++l) {
+        s[l] = (l == 0) ? 1.0 : std::pow(alpha, (double)l / L);
+        sinv[l] = ((l == 0) ? 1.0 : std::pow(alpha, -(double)l / L)) / L;
+        isw[l] = (float)(1.0 / (s[l] * wscale));
+        for (int m = 0; m < M; ++m)
+            for (int j = 0; j < M; ++j)
+                qs[((size_t)l * M + m) * M + j] =
+                    s[l] * p->dT * (transposed ? p->Q[j * M + m] : p->Q[m * M + j]);
+    }
+    std::vector<cd> mu((size_t)F * M), Sinv((size_t)F * M * M), P((size_t)F * M * M);
+    double worst = ac::freq_tables(M, L, alpha, transposed != 0, p->Q, p->t, mu.data(), Sinv.data(),
+                                   P.data(), nullptr);
+    if (worst < 0 || worst > 1e10)
+        return fail(AC_ERR_NOT_DIAGONALIZABLE, "Q G_l^{-1} not diagonalisable for alpha=%g (cond %g)", alpha,
+                    worst);
+    for (auto& v : mu) v *= p->dT;
+    CK(cudaMemcpyAsync(p->d_qs, qs.data(), qs.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(p->d_s, s.data(), s.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(p->d_sinv, sinv.data(), sinv.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(p->d_inv_s_w, isw.data(), isw.size() * sizeof(float), cudaMemcpyHostToDevice, st));
+    CK(upload_c(p, p->d_Sinv, Sinv.data(), Sinv.size(), st));
+    CK(upload_c(p, p->d_P, P.data(), P.size(), st));
+    CK(upload_c(p, p->d_mu, mu.data(), mu.size(), st));
+    p->cur_alpha = alpha;
+    p->cur_transposed = transposed;
+    p->cur_wscale = wscale;
+    return AC_OK;
+}
+
+// ------------------------------------------------------ one preconditioner
+// out (+)= C_alpha^{-1} (w - C u)   [u may be null: out (+)= C_alpha^{-1} w]
+template <typename R>
+static int stage_a(ac_plan* p, const double* u, const double* u0, const double* b, int b_rev, int transposed,
+                   cudaStream_t st, bool record_res) {
+    ac::FwdArgs fa;
+    fa.g = transposed ? p->grid_adj : p->grid_fwd;
+    fa.M = p->M;
+    fa.L = p->L;
+    fa.logL = p->logL;
+    fa.F = p->F;
+    fa.P = p->P;
+    fa.u = u;
+    fa.u0 = u0;
+    fa.b = b;
+    fa.b_reversed = b_rev;
+    fa.transposed = transposed;
+    fa.qs = p->d_qs;
+    fa.s = p->d_s;
+    fa.inv_s_w = p->d_inv_s_w;
+    fa.tw = p->tw_L;
+    fa.Sinv = p->d_Sinv;
+    fa.X = p->X;
+    fa.part = p->d_part_fwd;
+    const size_t smem = (size_t)p->L * p->M * p->P * sizeof(R);
+    {
+        ProfScope ps(p, KK_FWD, st);
+        CK(ac::launch_fwd<R>(fa, p->grid, smem, st));
+        p->launches++;
+    }
+    if (record_res) {
+        CK(cudaMemcpyAsync(p->h_part_fwd, p->d_part_fwd, sizeof(float) * p->grid, cudaMemcpyDeviceToHost, st));
+        CK(cudaEventRecord(p->ev_res, st));
+    }
+    ac::SpaceArgs sa;
+    sa.nx = p->prob.nx;
+    sa.ny = p->prob.dim == 2 ? p->prob.ny : 1;
+    sa.lognx = ilog2(sa.nx);
+    sa.logny = ilog2(sa.ny);
+    sa.planes = p->F * p->M;
+    sa.M = p->M;
+    sa.X = p->X;
+    sa.mu_dT = p->d_mu;
+    sa.sig_x = transposed ? p->sigT_x : p->sig_x;
+    sa.sig_y = transposed ? p->sigT_y : p->sig_y;
+    sa.tw_x = p->tw_x;
+    sa.tw_y = p->tw_y;
+    sa.rows_per_block = p->rows_per_block;
+    sa.cols_per_block = p->cols_per_block;
+    {
+        ProfScope ps(p, KK_SPACE, st);
+        if (p->spatial_path == 0) {
+            CK(ac::launch_space_1d<R>(sa, st));
+            p->launches++;
+        } else if (p->spatial_path == 1) {
+            CK(ac::launch_space_2d_small<R>(sa, st));
+            p->launches++;
+        } else if (p->spatial_path == 2) {
+            CK(ac::launch_space_rows<R>(sa, 0, st));
+            CK(ac::launch_space_cols<R>(sa, st));
+            CK(ac::launch_space_rows<R>(sa, 1, st));
+            p->launches += 3;
+        } else {
+            return fail(AC_ERR_INVALID_ARG, "inner solver path %d not available", p->spatial_path);
+        }
+    }
+    return AC_OK;
+}
+
+template <typename R>
+static int stage_b(ac_plan* p, double* out, int accumulate, cudaStream_t st) {
+    const size_t smem = (size_t)p->L * p->M * p->P * sizeof(R);
+    ac::UpdArgs ua;
+    ua.N = p->N;
+    ua.M = p->M;
+    ua.L = p->L;
+    ua.logL = p->logL;
+    ua.F = p->F;
+    ua.P = p->P;
+    ua.X = p->X;
+    ua.Pm = p->d_P;
+    ua.tw = p->tw_L;
+    ua.sinv = p->d_sinv;
+    ua.out = out;
+    ua.accumulate = accumulate;
+    ua.part = p->d_part_upd;
+    {
+        ProfScope ps(p, KK_UPD, st);
+        CK(ac::launch_upd<R>(ua, p->grid, smem, st));
+        p->launches++;
+    }
+    return AC_OK;
+}
+
+static int precond_a(ac_plan* p, const double* u, const double* u0, const double* b, int b_rev, int transposed,
+                     cudaStream_t st, bool record_res) {
+    if (p->precision == AC_C128) return stage_a<double>(p, u, u0, b, b_rev, transposed, st, record_res);
+    return stage_a<float>(p, u, u0, b, b_rev, transposed, st, record_res);
+}
+
+static int precond_b(ac_plan* p, double* out, int accumulate, cudaStream_t st) {
+    if (p->precision == AC_C128) return stage_b<double>(p, out, accumulate, st);
+    return stage_b<float>(p, out, accumulate, st);
+}
+
+static int precond(ac_plan* p, const double* u, const double* u0, const double* b, int b_rev, int transposed,
+                   double* out, int accumulate, cudaStream_t st, bool record_res) {
+    int rc = precond_a(p, u, u0, b, b_rev, transposed, st, record_res);
+    if (rc) return rc;
+    return precond_b(p, out, accumulate, st);
+}
+
+// ||w||_2 and ||w||_inf with w = (u0 stacked in block 0) + b
+static int w_norms(ac_plan* p, const double* u0, const double* b, double* n2, double* ninf, cudaStream_t st) {
+    const int grid = 152 * 2;
+    {
+        ProfScope ps(p, KK_AUX, st);
+        CK(ac::launch_wnorms(u0, b, p->L, p->M, p->N, p->d_part_d, grid, st));
+        p->launches++;
+    }
+    CK(cudaMemcpyAsync(p->h_part_d, p->d_part_d, sizeof(double) * 2 * grid, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    double s = 0.0, mx = 0.0;
+    for (int i = 0; i < grid; ++i) {
+        s += p->h_part_d[2 * i];
+        mx = std::max(mx, p->h_part_d[2 * i + 1]);
+    }
+    *n2 = std::sqrt(s);
+    *ninf = mx;
+    return AC_OK;
+}
+
+static double a_inf_norm(const ac_plan* p) {
+    double s = 0.0;
+    for (int i = 0; i < 5; ++i) {
+        if (i == 2) continue;
+        s += std::fabs(p->grid_fwd.tx[i]) + (p->prob.dim == 2 ? std::fabs(p->grid_fwd.ty[i]) : 0.0);
+    }
+    return s + std::fabs(p->grid_fwd.c0);
+}
+
+static double pow2_scale(double v) {
+    if (!(v > 0.0) || !std::isfinite(v)) return 1.0;
+    int e;
+    std::frexp(v, &e);
+    return std::ldexp(1.0, e);
+}
+
+// The Richardson loop shared by the forward and the adjoint solve.
+static int richardson_loop(ac_plan* p, const double* u0, const double* b, int b_rev, int transposed, double* u,
+                           double tol, ac_stats* stats, cudaStream_t st) {
+    ac_stats local;
+    ac_stats* S = stats ? stats : &local;
+    std::memset(S, 0, sizeof(ac_stats));
+    double wn2 = 0, winf = 0;
+    int rc = w_norms(p, u0, b, &wn2, &winf, st);
+    if (rc) return rc;
+    S->w_norm2 = wn2;
+    S->w_inf = winf;
+    if (!std::isfinite(wn2)) return fail(AC_ERR_NOT_FINITE, "right-hand side is not finite");
+    if (wn2 == 0.0) {
+        CK(cudaMemsetAsync(u, 0, sizeof(double) * (size_t)p->L * p->M * p->N, st));
+        S->converged = 1;
+        return AC_OK;
+    }
+    const double wscale = pow2_scale(winf);
+    const ac_alpha_schedule& sc = p->sched;
+    const int max_iter = std::min(std::max(sc.max_iter, 1), AC_MAX_STATS - 1);
+    const double eps = p->precision == AC_C128 ? std::ldexp(1.0, -53) : std::ldexp(1.0, -24);
+    const double tau = p->inner == AC_INNER_BICGSTAB ? sc.tau : 0.0;
+    const double gam = p->L * (3.0 * eps + tau) * winf;
+    double m = sc.m0 > 0 ? sc.m0 : p->L * p->dT * a_inf_norm(p) * winf;
+    const double alpha_mixed = std::min(0.25, std::max(1e-8, std::sqrt(p->L * (3.0 * eps + tau))));
+    int grew = 0;
+    double prev_res = 1e300;
+    for (int k = 0;; ++k) {
+        double alpha;
+        double m_next = 0.0;
+        if (sc.mode == AC_ALPHA_FIXED) alpha = sc.alpha0;
+        else if (sc.mode == AC_ALPHA_MIXED) alpha = alpha_mixed;
+        else {
+            alpha = std::sqrt(gam / m);          // alpha_{k+1} = sqrt(gamma / m_k)
+            m_next = 2.0 * std::sqrt(m * gam);   // m_{k+1} = 2 sqrt(m_k gamma)
+            alpha = std::min(0.5, std::max(alpha, 1e-12));
+        }
+        rc = ensure_tables(p, alpha, transposed, wscale, st);
+        if (rc) return rc;
+        // residual of u^(k), transform and spatial solve; the host reads the
+        // residual norm while the spatial solve runs and only then queues the
+        // update, so a converged u^(k) is returned unchanged
+        rc = precond_a(p, u, u0, b, b_rev, transposed, st, true);
+        if (rc) return rc;
+        CK(cudaEventSynchronize(p->ev_res));
+        double s = 0.0;
+        for (int i = 0; i < p->grid; ++i) s += p->h_part_fwd[i];
+        const double res = std::sqrt(s) * wscale / wn2;
+        S->res_rel[k] = res;
+        S->m[k] = sc.mode == AC_ALPHA_PAPER ? m : 0.0;
+        S->iters = k;
+        if (!std::isfinite(res)) {
+            CK(cudaStreamSynchronize(st));
+            return fail(AC_ERR_NOT_FINITE, "residual norm not finite at iteration %d", k);
+        }
+        bool done = false;
+        if (sc.stop_rule == AC_STOP_RESIDUAL && res <= tol) done = true;
+        if (sc.stop_rule == AC_STOP_PAPER && k > 0 && (S->diff_last[k - 1] <= tol || m <= tol)) done = true;
+        if (done) {
+            S->converged = 1;
+            break;
+        }
+        if (k >= max_iter) break;
+        if (res > prev_res) {
+            if (++grew >= 3) {
+                CK(cudaStreamSynchronize(st));
+                return fail(AC_ERR_NO_CONVERGENCE, "residual grew three times in a row (iteration %d)", k);
+            }
+        } else grew = 0;
+        prev_res = res;
+        S->alpha[k] = alpha;
+        rc = precond_b(p, u, 1, st);
+        if (rc) return rc;
+        if (sc.mode == AC_ALPHA_PAPER) m = m_next;
+        if (sc.stop_rule == AC_STOP_PAPER) {
+            CK(cudaMemcpyAsync(p->h_part_upd, p->d_part_upd, sizeof(float) * p->grid, cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            float mx = 0.f;
+            for (int i = 0; i < p->grid; ++i) mx = std::max(mx, p->h_part_upd[i]);
+            S->diff_last[k] = mx;
+        }
+    }
+    CK(cudaStreamSynchronize(st));
+    return S->converged ? AC_OK : fail(AC_ERR_NO_CONVERGENCE, "stop rule not met after %d iterations", S->iters);
+}
+
+// --------------------------------------------------------------- C ABI
+extern "C" {
+
+const char* ac_status_string(int s) {
+    switch (s) {
+        case AC_OK: return "ok";
+        case AC_ERR_INVALID_ARG: return "invalid argument";
+        case AC_ERR_NOT_DIAGONALIZABLE: return "Q G_l^{-1} not diagonalisable";
+        case AC_ERR_NO_CONVERGENCE: return "no convergence";
+        case AC_ERR_INNER_BREAKDOWN: return "inner solver breakdown";
+        case AC_ERR_CUDA: return "CUDA error";
+        case AC_ERR_NOT_FINITE: return "non-finite value";
+    }
+    return "unknown status";
+}
+
+const char* ac_last_error(void) { return g_err.c_str(); }
+
+void ac_destroy(ac_plan* p) {
+    if (!p) return;
+    drain_profile(p);
+    for (auto e : p->pool) cudaEventDestroy(e);
+    void* bufs[] = {p->X, p->tw_L, p->tw_x, p->tw_y, p->sig_x, p->sig_y, p->sigT_x, p->sigT_y,
+                    p->d_qs, p->d_s, p->d_inv_s_w, p->d_sinv, p->d_Sinv, p->d_P, p->d_mu,
+                    p->d_part_fwd, p->d_part_upd, p->d_part_d, p->d_dtQ, p->d_dtQT};
+    for (void* b : bufs)
+        if (b) cudaFree(b);
+    if (p->h_part_fwd) cudaFreeHost(p->h_part_fwd);
+    if (p->h_part_upd) cudaFreeHost(p->h_part_upd);
+    if (p->h_part_d) cudaFreeHost(p->h_part_d);
+    if (p->ev_res) cudaEventDestroy(p->ev_res);
+    delete p;
+}
+
+int ac_setup(const ac_problem* prob, int M, int L, double dT, const ac_alpha_schedule* sched, int precision,
+             int inner, ac_plan** out) {
+    if (!prob || !sched || !out) return fail(AC_ERR_INVALID_ARG, "null argument");
+    *out = nullptr;
+    if (prob->dim != 1 && prob->dim != 2) return fail(AC_ERR_INVALID_ARG, "dim must be 1 or 2");
+    if (prob->order != 2 && prob->order != 4) return fail(AC_ERR_INVALID_ARG, "order must be 2 or 4");
+    const int ny = prob->dim == 2 ? prob->ny : 1;
+    if (prob->nx < 2 || ny < 1 || (prob->dim == 2 && ny < 2))
+        return fail(AC_ERR_INVALID_ARG, "grid too small");
+    if (M < 1 || M > 4) return fail(AC_ERR_INVALID_ARG, "M must be 1..4");
+    if (!is_pow2(L) || L < 2 || L > 1024) return fail(AC_ERR_INVALID_ARG, "L must be a power of two in 2..1024");
+    if (!(dT > 0)) return fail(AC_ERR_INVALID_ARG, "dT must be positive");
+    if (precision != AC_C128 && precision != AC_C64) return fail(AC_ERR_INVALID_ARG, "bad precision");
+    if (inner != AC_INNER_FFT && inner != AC_INNER_BICGSTAB) return fail(AC_ERR_INVALID_ARG, "bad inner solver");
+    if (!(prob->lx > 0) || (prob->dim == 2 && !(prob->ly > 0))) return fail(AC_ERR_INVALID_ARG, "bad box length");
+    const long long Nll = (long long)prob->nx * ny;
+    if (Nll > (1LL << 30)) return fail(AC_ERR_INVALID_ARG, "grid too large");
+
+    ac_plan* p = new ac_plan();
+    p->prob = *prob;
+    p->prob.ny = ny;
+    p->M = M;
+    p->L = L;
+    p->logL = ilog2(L);
+    p->F = L / 2 + 1;
+    p->N = (int)Nll;
+    p->dT = dT;
+    p->sched = *sched;
+    p->precision = precision;
+    p->inner = inner;
+    p->csize = precision == AC_C128 ? 16 : 8;
+    cudaGetDevice(&p->device);
+    ac::radau_nodes(M, p->t);
+    ac::collocation_matrix(M, p->t, p->Q);
+
+    // stencil taps of A and A^T
+    double tx[5] = {0}, ty[5] = {0};
+    ac::axis_taps(prob->order, prob->nx, prob->lx, prob->nu, prob->cx, tx);
+    if (prob->dim == 2) ac::axis_taps(prob->order, ny, prob->ly, prob->nu, prob->cy, ty);
+    ac::Grid g;
+    g.dim = prob->dim;
+    g.nx = prob->nx;
+    g.ny = ny;
+    g.N = p->N;
+    g.rad = prob->order == 4 ? 2 : 1;
+    for (int i = 0; i < 5; ++i) {
+        g.tx[i] = tx[i];
+        g.ty[i] = ty[i];
+    }
+    g.c0 = tx[2] + ty[2];
+    p->grid_fwd = g;
+    for (int i = 0; i < 5; ++i) {
+        g.tx[i] = tx[4 - i];
+        g.ty[i] = ty[4 - i];
+    }
+    p->grid_adj = g;
+    {
+        double d1[5], d2[5];
+        ac::central_coeffs(prob->order, d1, d2);
+        const double hx = prob->lx / prob->nx, hy = prob->dim == 2 ? prob->ly / ny : 1.0;
+        for (int i = 0; i < 5; ++i) {
+            p->d1x[i] = d1[i] / hx;
+            p->d2x[i] = d2[i] / (hx * hx);
+            p->d1y[i] = prob->dim == 2 ? d1[i] / hy : 0.0;
+            p->d2y[i] = prob->dim == 2 ? d2[i] / (hy * hy) : 0.0;
+        }
+    }
+
+    // spatial solve path
+    const size_t cs = p->csize;
+    if (inner == AC_INNER_FFT) {
+        if (!is_pow2(prob->nx) || !is_pow2(ny)) {
+            ac_destroy(p);
+            return fail(AC_ERR_INVALID_ARG, "the FFT inner solver needs power-of-two grid sizes");
+        }
+        if (prob->dim == 1) {
+            if ((size_t)prob->nx * cs > 160 * 1024) {
+                ac_destroy(p);
+                return fail(AC_ERR_INVALID_ARG, "1D grid too large for the one-CTA FFT solve");
+            }
+            p->spatial_path = 0;
+        } else if ((size_t)prob->nx * ny * cs <= 160 * 1024) {
+            p->spatial_path = 1;
+        } else {
+            p->spatial_path = 2;
+            int rpb = std::max(1, (int)(32768 / ((size_t)prob->nx * cs)));
+            while (rpb & (rpb - 1)) rpb &= rpb - 1;
+            p->rows_per_block = std::min(rpb, ny);
+            int W = (int)(128 / cs);
+            if (W > prob->nx) W = prob->nx;
+            p->cols_per_block = W;
+            if ((size_t)prob->nx * cs > 160 * 1024 || (size_t)ny * W * cs > 160 * 1024) {
+                ac_destroy(p);
+                return fail(AC_ERR_INVALID_ARG, "2D grid too large for the three-pass FFT solve");
+            }
+        }
+    } else {
+        ac_destroy(p);
+        return fail(AC_ERR_INVALID_ARG, "BiCGStab inner solver not built into this library");
+    }
+
+    // tile of the time kernels: P points, L*M*P reals of shared memory
+    const size_t rsz = cs / 2;
+    int P = 256;
+    while (P > 2 && (size_t)L * M * P * rsz > 100 * 1024) P >>= 1;
+    while (P > 16 && (p->N + P - 1) / P < 2 * 152) P >>= 1;
+    if ((size_t)L * M * P * rsz > 200 * 1024) {
+        ac_destroy(p);
+        return fail(AC_ERR_INVALID_ARG, "L*M too large for the shared-memory time transform");
+    }
+    p->P = P;
+    p->grid = (p->N + P - 1) / P;
+
+    // device buffers
+    cudaError_t e = cudaSuccess;
+#define AL(ptr, bytes)                                                  \
+    do {                                                                \
+        if (e == cudaSuccess) e = dalloc(p, &(ptr), (bytes));           \
+    } while (0)
+    const int F = p->F;
+    AL(p->X, (size_t)F * M * p->N * cs);
+    AL(p->tw_L, (size_t)std::max(1, L / 2) * cs);
+    AL(p->tw_x, (size_t)std::max(1, prob->nx / 2) * cs);
+    AL(p->tw_y, (size_t)std::max(1, ny / 2) * cs);
+    AL(p->sig_x, (size_t)prob->nx * cs);
+    AL(p->sig_y, (size_t)ny * cs);
+    AL(p->sigT_x, (size_t)prob->nx * cs);
+    AL(p->sigT_y, (size_t)ny * cs);
+    AL(p->d_qs, sizeof(double) * (size_t)L * M * M);
+    AL(p->d_s, sizeof(double) * L);
+    AL(p->d_inv_s_w, sizeof(float) * L);
+    AL(p->d_sinv, sizeof(double) * L);
+    AL(p->d_Sinv, (size_t)F * M * M * cs);
+    AL(p->d_P, (size_t)F * M * M * cs);
+    AL(p->d_mu, (size_t)F * M * cs);
+    AL(p->d_part_fwd, sizeof(float) * p->grid);
+    AL(p->d_part_upd, sizeof(float) * p->grid);
+    p->part_d_len = std::max(2 * 152 * 2, 3 * 152 * 4);
+    AL(p->d_part_d, sizeof(double) * p->part_d_len);
+    AL(p->d_dtQ, sizeof(double) * M * M);
+    AL(p->d_dtQT, sizeof(double) * M * M);
+#undef AL
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&p->h_part_fwd, sizeof(float) * p->grid);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&p->h_part_upd, sizeof(float) * p->grid);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&p->h_part_d, sizeof(double) * p->part_d_len);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_res, cudaEventBlockingSync);
+    if (e != cudaSuccess) {
+        int rc = fail(AC_ERR_CUDA, "allocation failed: %s", cudaGetErrorString(e));
+        ac_destroy(p);
+        return rc;
+    }
+    // constant tables
+    std::vector<cd> tw, sx(prob->nx), sy(ny), sxT(prob->nx), syT(ny);
+    int rc = AC_OK;
+    auto up = [&](void* dst, const std::vector<cd>& v) {
+        if (rc == AC_OK && upload_c(p, dst, v.data(), v.size(), 0) != cudaSuccess)
+            rc = fail(AC_ERR_CUDA, "table upload failed");
+    };
+    twiddles(L, tw);
+    up(p->tw_L, tw);
+    twiddles(prob->nx, tw);
+    up(p->tw_x, tw);
+    twiddles(ny, tw);
+    up(p->tw_y, tw);
+    ac::axis_symbol(prob->nx, p->grid_fwd.tx, sx.data());
+    ac::axis_symbol(prob->nx, p->grid_adj.tx, sxT.data());
+    if (prob->dim == 2) {
+        ac::axis_symbol(ny, p->grid_fwd.ty, sy.data());
+        ac::axis_symbol(ny, p->grid_adj.ty, syT.data());
+    } else {
+        sy.assign(ny, cd(0.0));
+        syT.assign(ny, cd(0.0));
+    }
+    up(p->sig_x, sx);
+    up(p->sig_y, sy);
+    up(p->sigT_x, sxT);
+    up(p->sigT_y, syT);
+    double dtQ[64], dtQT[64];
+    for (int m = 0; m < M; ++m)
+        for (int j = 0; j < M; ++j) {
+            dtQ[m * M + j] = dT * p->Q[m * M + j];
+            dtQT[m * M + j] = dT * p->Q[j * M + m];
+        }
+    if (rc == AC_OK && (cudaMemcpy(p->d_dtQ, dtQ, sizeof(double) * M * M, cudaMemcpyHostToDevice) != cudaSuccess ||
+                        cudaMemcpy(p->d_dtQT, dtQT, sizeof(double) * M * M, cudaMemcpyHostToDevice) != cudaSuccess))
+        rc = fail(AC_ERR_CUDA, "table upload failed");
+    if (rc == AC_OK && cudaDeviceSynchronize() != cudaSuccess) rc = fail(AC_ERR_CUDA, "set-up sync failed");
+    if (rc != AC_OK) {
+        ac_destroy(p);
+        return rc;
+    }
+    *out = p;
+    return AC_OK;
+}
+
+int ac_plan_get_info(const ac_plan* p, ac_plan_info* info) {
+    if (!p || !info) return fail(AC_ERR_INVALID_ARG, "null argument");
+    info->N = p->N;
+    info->M = p->M;
+    info->L = p->L;
+    info->F = p->F;
+    info->tile_fwd = p->P;
+    info->tile_upd = p->P;
+    info->spatial_path = p->spatial_path;
+    info->workspace_bytes = p->workspace;
+    info->launches = p->launches;
+    return AC_OK;
+}
+
+static int apply_impl(ac_plan* p, const double* u, double* out, int transposed, void* stream) {
+    if (!p || !u || !out) return fail(AC_ERR_INVALID_ARG, "null argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    ac::ApplyArgs a;
+    a.g = transposed ? p->grid_adj : p->grid_fwd;
+    a.M = p->M;
+    a.L = p->L;
+    a.transposed = transposed;
+    a.u = u;
+    a.out = out;
+    a.dtQ = transposed ? p->d_dtQT : p->d_dtQ;
+    ProfScope ps(p, KK_APPLY, st);
+    CK(ac::launch_apply(a, st));
+    p->launches++;
+    return AC_OK;
+}
+
+int ac_apply_C(ac_plan* p, const double* u, double* Cu, void* stream) { return apply_impl(p, u, Cu, 0, stream); }
+int ac_apply_CT(ac_plan* p, const double* lam, double* out, void* stream) {
+    return apply_impl(p, lam, out, 1, stream);
+}
+
+int ac_precond_solve(ac_plan* p, double alpha, const double* r, double* e, void* stream) {
+    if (!p || !r || !e) return fail(AC_ERR_INVALID_ARG, "null argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = ensure_tables(p, alpha, 0, p->cur_wscale > 0 ? p->cur_wscale : 1.0, st);
+    if (rc) return rc;
+    return precond(p, nullptr, nullptr, r, 0, 0, e, 0, st, false);
+}
+
+int ac_richardson_step(ac_plan* p, double alpha, const double* u0, const double* b, double* u,
+                       double* res_rel_out, void* stream) {
+    if (!p || !u) return fail(AC_ERR_INVALID_ARG, "null argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    double wn2 = 1.0, winf = 1.0;
+    if (res_rel_out) {
+        int rc = w_norms(p, u0, b, &wn2, &winf, st);
+        if (rc) return rc;
+    }
+    const double wscale = res_rel_out ? pow2_scale(winf) : (p->cur_wscale > 0 ? p->cur_wscale : 1.0);
+    int rc = ensure_tables(p, alpha, 0, wscale, st);
+    if (rc) return rc;
+    rc = precond(p, u, u0, b, 0, 0, u, 1, st, res_rel_out != nullptr);
+    if (rc) return rc;
+    if (res_rel_out) {
+        CK(cudaEventSynchronize(p->ev_res));
+        double s = 0.0;
+        for (int i = 0; i < p->grid; ++i) s += p->h_part_fwd[i];
+        *res_rel_out = wn2 > 0 ? std::sqrt(s) * wscale / wn2 : std::sqrt(s) * wscale;
+    }
+    return AC_OK;
+}
+
+int ac_richardson_solve(ac_plan* p, const double* u0, const double* b, double* u, int init_u, double tol,
+                        ac_stats* stats, void* stream) {
+    if (!p || !u) return fail(AC_ERR_INVALID_ARG, "null argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!init_u) {
+        ProfScope ps(p, KK_AUX, st);
+        CK(ac::launch_fill_stack(u0, u, p->L, p->M, p->N, st));
+        p->launches++;
+    }
+    return richardson_loop(p, u0, b, 0, 0, u, tol, stats, st);
+}
+
+int ac_adjoint_solve(ac_plan* p, const double* g, double* lam, double tol, ac_stats* stats, void* stream) {
+    if (!p || !g || !lam || g == lam) return fail(AC_ERR_INVALID_ARG, "bad argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    // solve in reversed time: lam'[l] = lam[L-1-l], rhs g'[l] = g[L-1-l]
+    CK(cudaMemsetAsync(lam, 0, sizeof(double) * (size_t)p->L * p->M * p->N, st));
+    int rc = richardson_loop(p, nullptr, g, 1, 1, lam, tol, stats, st);
+    if (rc != AC_OK && rc != AC_ERR_NO_CONVERGENCE) return rc;
+    {
+        ProfScope ps(p, KK_AUX, st);
+        cudaError_t e = ac::launch_reverse_time(lam, p->L, (long long)p->M * p->N, st);
+        if (e != cudaSuccess) return fail(AC_ERR_CUDA, "reverse failed: %s", cudaGetErrorString(e));
+        p->launches++;
+    }
+    return rc;
+}
+
+int ac_grad_params(ac_plan* p, const double* u, const double* lam, double* du0, double* dparams, void* stream) {
+    if (!p || !u || !lam || !dparams) return fail(AC_ERR_INVALID_ARG, "null argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    ac::GradArgs a;
+    a.g = p->grid_fwd;
+    a.M = p->M;
+    a.L = p->L;
+    a.u = u;
+    a.lam = lam;
+    a.dtQ = p->d_dtQ;
+    for (int i = 0; i < 5; ++i) {
+        a.d2x[i] = p->d2x[i];
+        a.d1x[i] = p->d1x[i];
+        a.d2y[i] = p->d2y[i];
+        a.d1y[i] = p->d1y[i];
+    }
+    a.part = p->d_part_d;
+    const int grid = std::min(p->part_d_len / 3, 152 * 4);
+    {
+        ProfScope ps(p, KK_GRAD, st);
+        CK(ac::launch_grad(a, grid, st));
+        p->launches++;
+    }
+    if (du0) {
+        ProfScope ps(p, KK_GRAD, st);
+        CK(ac::launch_sum_blocks(lam, p->M, p->N, du0, st));
+        p->launches++;
+    }
+    CK(cudaMemcpyAsync(p->h_part_d, p->d_part_d, sizeof(double) * 3 * grid, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    double s[3] = {0, 0, 0};
+    for (int i = 0; i < grid; ++i)
+        for (int c = 0; c < 3; ++c) s[c] += p->h_part_d[3 * i + c];
+    dparams[0] = s[0];
+    dparams[1] = -s[1];
+    dparams[2] = p->prob.dim == 2 ? -s[2] : 0.0;
+    return AC_OK;
+}
+
+int ac_profile_enable(ac_plan* p, int on) {
+    if (!p) return fail(AC_ERR_INVALID_ARG, "null plan");
+    drain_profile(p);
+    p->prof = on != 0;
+    for (int k = 0; k < KK_COUNT; ++k) {
+        p->prof_ms[k] = 0;
+        p->prof_count[k] = 0;
+    }
+    return AC_OK;
+}
+
+int ac_profile_read(ac_plan* p, int cap, const char** names, double* ms, long long* count) {
+    if (!p) return fail(AC_ERR_INVALID_ARG, "null plan");
+    drain_profile(p);
+    const int n = std::min(cap, (int)KK_COUNT);
+    for (int k = 0; k < n; ++k) {
+        if (names) names[k] = kKindNames[k];
+        if (ms) ms[k] = p->prof_ms[k];
+        if (count) count[k] = p->prof_count[k];
+    }
+    return KK_COUNT;
+}
+
+}  // extern "C"

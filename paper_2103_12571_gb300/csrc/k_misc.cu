@@ -1,0 +1,259 @@
+// FP64 operator and reduction kernels around the Richardson iteration:
+// C u and C^T u (eq. (globalsys)), the gradient contractions of the adjoint,
+// norms of the right-hand side w, and small helpers.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace ac {
+
+struct Nbr {
+    int dx[4], dy[4];  // offsets -1, +1, -2, +2 as deltas of the flat index
+};
+
+__device__ __forceinline__ Nbr neighbours(const Grid& g, long n) {
+    Nbr b;
+    const int nx = g.nx;
+    const long iy = n / nx;
+    const int ix = (int)(n - iy * nx);
+    const int offs[4] = {-1, 1, -2, 2};
+#pragma unroll
+    for (int o = 0; o < 4; ++o) {
+        int jx = ix + offs[o];
+        jx = jx < 0 ? jx + nx : (jx >= nx ? jx - nx : jx);
+        b.dx[o] = jx - ix;
+        b.dy[o] = 0;
+        if (g.dim == 2) {
+            long jy = iy + offs[o];
+            jy = jy < 0 ? jy + g.ny : (jy >= g.ny ? jy - g.ny : jy);
+            b.dy[o] = (int)((jy - iy) * nx);
+        }
+    }
+    return b;
+}
+
+// sum_o tx[o] v(x+o) + ty[o] v(y+o) with the centre tap c
+__device__ __forceinline__ double stencil(const double* v, const Nbr& b, int rad, int dim,
+                                          const double* tx, const double* ty, double c) {
+    double acc = c * v[0];
+#pragma unroll
+    for (int o = 0; o < 4; ++o) {
+        if (o < 2 * rad) {
+            const int tap = (o == 0) ? 1 : (o == 1) ? 3 : (o == 2) ? 0 : 4;
+            acc = fma(tx[tap], v[b.dx[o]], acc);
+            if (dim == 2) acc = fma(ty[tap], v[b.dy[o]], acc);
+        }
+    }
+    return acc;
+}
+
+// out = C u (transposed = 0) or C^T u (transposed = 1; then dtQ holds dT Q^T
+// and the taps those of A^T), natural time order.
+__global__ void k_apply(ApplyArgs a) {
+    const long N = a.g.N;
+    const int M = a.M;
+    const long total = (long)a.L * N;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+        const int l = (int)(t / N);
+        const long n = t - (long)l * N;
+        const Nbr b = neighbours(a.g, n);
+        double Au[8];
+        const double* ub = a.u + (long)l * M * N + n;
+        for (int j = 0; j < M; ++j)
+            Au[j] = stencil(ub + (long)j * N, b, a.g.rad, a.g.dim, a.g.tx, a.g.ty, a.g.c0);
+        double coup_all = 0.0, coup_last = 0.0;
+        if (!a.transposed) {
+            if (l > 0) coup_all = ub[-(long)N];                       // u_{l-1,M}
+        } else {
+            if (l + 1 < a.L)
+                for (int j = 0; j < M; ++j) coup_last += ub[(long)(M + j) * N];  // sum_j u_{l+1,j}
+        }
+        for (int m = 0; m < M; ++m) {
+            double v = ub[(long)m * N] - coup_all - (m == M - 1 ? coup_last : 0.0);
+            for (int j = 0; j < M; ++j) v = fma(-a.dtQ[m * M + j], Au[j], v);
+            a.out[((long)l * M + m) * N + n] = v;
+        }
+    }
+}
+
+// Partial sums of lam . (dT Q (x) D) u for D = Lap, D_x, D_y.
+__global__ void __launch_bounds__(256) k_grad(GradArgs a) {
+    __shared__ double red[32];
+    const long N = a.g.N;
+    const int M = a.M;
+    const long total = (long)a.L * N;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+        const int l = (int)(t / N);
+        const long n = t - (long)l * N;
+        const Nbr b = neighbours(a.g, n);
+        double Lu[8], Dx[8], Dy[8];
+        const double* ub = a.u + (long)l * M * N + n;
+        for (int j = 0; j < M; ++j) {
+            const double* v = ub + (long)j * N;
+            Lu[j] = stencil(v, b, a.g.rad, a.g.dim, a.d2x, a.d2y, a.d2x[2] + (a.g.dim == 2 ? a.d2y[2] : 0.0));
+            Dx[j] = stencil(v, b, a.g.rad, 1, a.d1x, a.d1x, a.d1x[2]);
+            Dy[j] = 0.0;
+            if (a.g.dim == 2) {
+                // y-derivative only: use the y offsets with the d1y taps
+                double acc = a.d1y[2] * v[0];
+                for (int o = 0; o < 2 * a.g.rad; ++o) {
+                    const int tap = (o == 0) ? 1 : (o == 1) ? 3 : (o == 2) ? 0 : 4;
+                    acc = fma(a.d1y[tap], v[b.dy[o]], acc);
+                }
+                Dy[j] = acc;
+            }
+        }
+        const double* lb = a.lam + (long)l * M * N + n;
+        for (int m = 0; m < M; ++m) {
+            double ql = 0.0, qx = 0.0, qy = 0.0;
+            for (int j = 0; j < M; ++j) {
+                const double q = a.dtQ[m * M + j];
+                ql = fma(q, Lu[j], ql);
+                qx = fma(q, Dx[j], qx);
+                qy = fma(q, Dy[j], qy);
+            }
+            const double lv = lb[(long)m * N];
+            s0 = fma(lv, ql, s0);
+            s1 = fma(lv, qx, s1);
+            s2 = fma(lv, qy, s2);
+        }
+    }
+    s0 = block_sum_d(s0, red);
+    if (threadIdx.x == 0) a.part[blockIdx.x * 3 + 0] = s0;
+    s1 = block_sum_d(s1, red);
+    if (threadIdx.x == 0) a.part[blockIdx.x * 3 + 1] = s1;
+    s2 = block_sum_d(s2, red);
+    if (threadIdx.x == 0) a.part[blockIdx.x * 3 + 2] = s2;
+}
+
+__global__ void k_sum_blocks(const double* lam, int M, long N, double* du0) {
+    for (long n = blockIdx.x * (long)blockDim.x + threadIdx.x; n < N; n += (long)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int m = 0; m < M; ++m) s += lam[(long)m * N + n];
+        du0[n] = s;
+    }
+}
+
+__global__ void k_reverse_time(double* v, int L, long blk) {
+    const long total = (long)(L / 2) * blk;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+        const int l = (int)(t / blk);
+        const long i = t - (long)l * blk;
+        double* a = v + (long)l * blk + i;
+        double* b = v + (long)(L - 1 - l) * blk + i;
+        const double x = *a;
+        *a = *b;
+        *b = x;
+    }
+}
+
+// per-block sum of squares (part[2b]) and max |v| (part[2b+1]) in FP64
+__global__ void __launch_bounds__(256) k_norms(const double* v, long n, double* part) {
+    __shared__ double red[32];
+    double s = 0.0, mx = 0.0;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const double x = v[i];
+        s = fma(x, x, s);
+        mx = fmax(mx, fabs(x));
+    }
+    s = block_sum_d(s, red);
+    if (threadIdx.x == 0) part[2 * blockIdx.x] = s;
+    // max via the same reduction tree
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double r = 0.0;
+        for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) r = fmax(r, red[w]);
+        part[2 * blockIdx.x + 1] = r;
+    }
+}
+
+cudaError_t launch_apply(const ApplyArgs& a, cudaStream_t st) {
+    long total = (long)a.L * a.g.N;
+    int grid = (int)((total + 255) / 256);
+    if (grid > 152 * 16) grid = 152 * 16;
+    k_apply<<<grid, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_grad(const GradArgs& a, int grid, cudaStream_t st) {
+    k_grad<<<grid, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sum_blocks(const double* lam, int M, int N, double* du0, cudaStream_t st) {
+    int grid = (N + 255) / 256;
+    if (grid > 152 * 8) grid = 152 * 8;
+    k_sum_blocks<<<grid, 256, 0, st>>>(lam, M, N, du0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reverse_time(double* v, int L, long long blk, cudaStream_t st) {
+    long total = (long)(L / 2) * blk;
+    if (total == 0) return cudaSuccess;
+    int grid = (int)((total + 255) / 256);
+    if (grid > 152 * 16) grid = 152 * 16;
+    k_reverse_time<<<grid, 256, 0, st>>>(v, L, blk);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_norms(const double* v, long long n, double* part, int grid, cudaStream_t st) {
+    k_norms<<<grid, 256, 0, st>>>(v, n, part);
+    return cudaGetLastError();
+}
+
+}  // namespace ac
+
+namespace ac {
+
+// sum of squares and max |w| of w = (u0 stacked over the M nodes of block 0) + b
+__global__ void __launch_bounds__(256) k_wnorms(const double* u0, const double* b, int L, int M, long N,
+                                                double* part) {
+    __shared__ double red[32];
+    const long total = b ? (long)L * M * N : (long)M * N;
+    double s = 0.0, mx = 0.0;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
+        const long blk = (long)M * N;
+        const long l = i / blk;
+        const long n = (i - l * blk) % N;
+        double w = b ? b[i] : 0.0;
+        if (l == 0 && u0) w += u0[n];
+        s = fma(w, w, s);
+        mx = fmax(mx, fabs(w));
+    }
+    s = block_sum_d(s, red);
+    if (threadIdx.x == 0) part[2 * blockIdx.x] = s;
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double r = 0.0;
+        for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) r = fmax(r, red[w]);
+        part[2 * blockIdx.x + 1] = r;
+    }
+}
+
+// u[l][m][n] = u0[n] (0 if u0 is null): the initial iterate of Sec. 5
+__global__ void k_fill_stack(const double* u0, double* u, long total, long N) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x)
+        u[i] = u0 ? u0[i % N] : 0.0;
+}
+
+cudaError_t launch_wnorms(const double* u0, const double* b, int L, int M, long long N, double* part, int grid,
+                          cudaStream_t st) {
+    k_wnorms<<<grid, 256, 0, st>>>(u0, b, L, M, N, part);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill_stack(const double* u0, double* u, int L, int M, long long N, cudaStream_t st) {
+    const long total = (long)L * M * N;
+    int grid = (int)((total + 255) / 256);
+    if (grid > 152 * 16) grid = 152 * 16;
+    k_fill_stack<<<grid, 256, 0, st>>>(u0, u, total, N);
+    return cudaGetLastError();
+}
+
+}  // namespace ac

@@ -1,0 +1,309 @@
+// Time-direction kernels of one Richardson iteration.
+//
+// k_fwd: step (i) FP64 residual r = w - C u of eq. (globalsys), step (ii) the
+//   alpha-scaling J^{-1} and the length-L FFT along time of eq. (s1)
+//   (Algorithm 1, lines computing r~ and x), and the node mixing
+//   x^1 = S_l^{-1} x of eq. (d1).  One CTA owns P grid points and all L*M
+//   values at each of them; the residual is written into shared memory in
+//   the transform precision, the FFT runs there (radix-2 DIF, bit-reversed
+//   output, which the per-frequency work does not care about), and only the
+//   F = L/2 + 1 non-redundant frequencies of the real data are stored.
+//   Two real columns are transformed as one complex column.
+// k_upd: eq. (d3) and (Gsubstitution) as one mix y = P_l x^2 with
+//   P_l = G_l^{-1} S_l, the inverse FFT along time of eq. (s3) (radix-2 DIT
+//   from bit-reversed order), the un-scaling by J, and the FP64 update
+//   u += e of the correction form of eq. (Riteration).
+#include "common.cuh"
+#include "kernels.h"
+
+namespace ac {
+
+template <int MM>
+__device__ __forceinline__ void residual_point(const FwdArgs& a, int l, long n, const int* dxo,
+                                               const int* dyo, double r[MM]) {
+    const Grid& g = a.g;
+    const long N = g.N;
+    const double s = a.s[l];
+    const int lb = a.b_reversed ? (a.L - 1 - l) : l;
+    if (!a.u) {
+#pragma unroll
+        for (int m = 0; m < MM; ++m) {
+            double w = (l == 0 && a.u0) ? a.u0[n] : 0.0;
+            if (a.b) w += a.b[((long)lb * MM + m) * N + n];
+            r[m] = s * w;
+        }
+        return;
+    }
+    const double* ub = a.u + (long)l * MM * N + n;
+    double uc[MM], Au[MM];
+#pragma unroll
+    for (int j = 0; j < MM; ++j) {
+        const double* uj = ub + (long)j * N;
+        uc[j] = uj[0];
+        double acc = g.c0 * uc[j];   // combined centre tap of both axes
+#pragma unroll
+        for (int o = 0; o < 4; ++o) {
+            if (o < 2 * g.rad) {
+                const int tap = (o == 0) ? 1 : (o == 1) ? 3 : (o == 2) ? 0 : 4;  // offsets -1,+1,-2,+2
+                acc = fma(g.tx[tap], uj[dxo[o]], acc);
+                if (g.dim == 2) acc = fma(g.ty[tap], uj[dyo[o]], acc);
+            }
+        }
+        Au[j] = acc;
+    }
+    const double* qs = a.qs + l * MM * MM;
+    double sp[MM];
+    if (!a.transposed) {
+        double c = 0.0;
+        if (l > 0) c = ub[-(long)N];                     // u_{l-1, M} (block l-1, last node)
+        if (l == 0 && a.u0) c += a.u0[n];
+#pragma unroll
+        for (int m = 0; m < MM; ++m) sp[m] = s * c;
+    } else {
+#pragma unroll
+        for (int m = 0; m < MM; ++m) sp[m] = 0.0;
+        if (l > 0) {
+            double c = 0.0;
+            const double* up = ub - (long)MM * N;
+#pragma unroll
+            for (int j = 0; j < MM; ++j) c += up[(long)j * N];  // (H^T u_{l-1})_M = sum_j u_{l-1,j}
+            sp[MM - 1] = s * c;
+        }
+        if (l == 0 && a.u0) {
+#pragma unroll
+            for (int m = 0; m < MM; ++m) sp[m] += a.u0[n];
+        }
+    }
+    if (a.b) {
+#pragma unroll
+        for (int m = 0; m < MM; ++m) sp[m] = fma(s, a.b[((long)lb * MM + m) * N + n], sp[m]);
+    }
+#pragma unroll
+    for (int m = 0; m < MM; ++m) {
+        double t = fma(-s, uc[m], sp[m]);
+#pragma unroll
+        for (int j = 0; j < MM; ++j) t = fma(qs[m * MM + j], Au[j], t);
+        r[m] = t;
+    }
+}
+
+template <typename R, int MM>
+__global__ void __launch_bounds__(256) k_fwd(FwdArgs a) {
+    typedef typename Cx<R>::T C;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ float red[32];
+    R* Zr = reinterpret_cast<R*>(smem_raw);
+    C* Z = reinterpret_cast<C*>(smem_raw);
+    const int P = a.P, HP = P >> 1;
+    const int logP = 31 - __clz(P);
+    const int L = a.L;
+    const long N = a.g.N;
+    const long n0 = (long)blockIdx.x * P;
+
+    // this thread's grid point is fixed (blockDim is a multiple of P)
+    const int p = threadIdx.x & (P - 1);
+    const long n = n0 + p;
+    int dxo[4] = {0, 0, 0, 0}, dyo[4] = {0, 0, 0, 0};
+    if (n < N) {
+        const int nx = a.g.nx;
+        const long iy = n / nx;
+        const int ix = (int)(n - iy * nx);
+        const int offs[4] = {-1, 1, -2, 2};
+#pragma unroll
+        for (int o = 0; o < 4; ++o) {
+            int jx = ix + offs[o];
+            jx = jx < 0 ? jx + nx : (jx >= nx ? jx - nx : jx);
+            dxo[o] = jx - ix;
+            if (a.g.dim == 2) {
+                long jy = iy + offs[o];
+                const int ny = a.g.ny;
+                jy = jy < 0 ? jy + ny : (jy >= ny ? jy - ny : jy);
+                dyo[o] = (int)((jy - iy) * nx);
+            }
+        }
+    }
+    float sq = 0.f;
+    for (int l = threadIdx.x >> logP; l < L; l += blockDim.x >> logP) {
+        double r[MM];
+        if (n < N) {
+            residual_point<MM>(a, l, n, dxo, dyo, r);
+            const float isw = a.inv_s_w[l];
+#pragma unroll
+            for (int m = 0; m < MM; ++m) {
+                const float rf = (float)r[m] * isw;
+                sq = fmaf(rf, rf, sq);
+            }
+        } else {
+#pragma unroll
+            for (int m = 0; m < MM; ++m) r[m] = 0.0;
+        }
+#pragma unroll
+        for (int m = 0; m < MM; ++m) Zr[((long)l * MM + m) * P + p] = (R)r[m];
+    }
+    __syncthreads();
+
+    const int nb = MM * HP;
+    const int lognb = (nb & (nb - 1)) == 0 ? 31 - __clz(nb) : -1;
+    fft_dif<C, true>(Z, a.logL, nb, lognb, nb, 1, reinterpret_cast<const C*>(a.tw));
+
+    const C* Sinv = reinterpret_cast<const C*>(a.Sinv);
+    C* X = reinterpret_cast<C*>(a.X);
+    const int logHP = logP - 1;
+    const R half = (R)0.5;
+    for (int idx = threadIdx.x; idx < a.F * HP; idx += blockDim.x) {
+        const int k = idx >> logHP, q = idx & (HP - 1);
+        const int pk = bitrev(k, a.logL), pn = bitrev((L - k) & (L - 1), a.logL);
+        const bool realbin = (k == 0) || (2 * k == L);
+        C A[MM], B[MM];
+#pragma unroll
+        for (int m = 0; m < MM; ++m) {
+            const C zk = Z[((long)pk * MM + m) * HP + q];
+            const C zn = Z[((long)pn * MM + m) * HP + q];
+            A[m] = cmake(half * (zk.x + zn.x), realbin ? (R)0 : half * (zk.y - zn.y));
+            B[m] = cmake(half * (zk.y + zn.y), realbin ? (R)0 : half * (zn.x - zk.x));
+        }
+        const C* S = Sinv + (long)k * MM * MM;
+        const long nn = n0 + 2 * q;
+#pragma unroll
+        for (int m = 0; m < MM; ++m) {
+            C xa = cmake((R)0, (R)0), xb = xa;
+#pragma unroll
+            for (int j = 0; j < MM; ++j) {
+                const C sm = S[m * MM + j];
+                xa = cfma(sm, A[j], xa);
+                xb = cfma(sm, B[j], xb);
+            }
+            C* dst = X + ((long)k * MM + m) * N + nn;
+            if (nn + 1 < N) { dst[0] = xa; dst[1] = xb; }
+            else if (nn < N) dst[0] = xa;
+        }
+    }
+    const float tot = block_sum(sq, red);
+    if (threadIdx.x == 0) a.part[blockIdx.x] = tot;
+}
+
+template <typename R, int MM>
+__global__ void __launch_bounds__(256) k_upd(UpdArgs a) {
+    typedef typename Cx<R>::T C;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ float red[32];
+    C* Z = reinterpret_cast<C*>(smem_raw);
+    const int P = a.P, HP = P >> 1;
+    const int logP = 31 - __clz(P), logHP = logP - 1;
+    const int L = a.L;
+    const long N = a.N;
+    const long n0 = (long)blockIdx.x * P;
+    const C* X = reinterpret_cast<const C*>(a.X);
+    const C* Pm = reinterpret_cast<const C*>(a.Pm);
+
+    for (int idx = threadIdx.x; idx < a.F * HP; idx += blockDim.x) {
+        const int k = idx >> logHP, q = idx & (HP - 1);
+        const long nn = n0 + 2 * q;
+        C xa[MM], xb[MM];
+#pragma unroll
+        for (int j = 0; j < MM; ++j) {
+            const C* src = X + ((long)k * MM + j) * N + nn;
+            xa[j] = nn < N ? src[0] : cmake((R)0, (R)0);
+            xb[j] = nn + 1 < N ? src[1] : cmake((R)0, (R)0);
+        }
+        const C* Pk = Pm + (long)k * MM * MM;
+        const bool realbin = (k == 0) || (2 * k == L);
+        const int pk = bitrev(k, a.logL), pn = bitrev((L - k) & (L - 1), a.logL);
+#pragma unroll
+        for (int m = 0; m < MM; ++m) {
+            C ya = cmake((R)0, (R)0), yb = ya;
+#pragma unroll
+            for (int j = 0; j < MM; ++j) {
+                const C pm = Pk[m * MM + j];
+                ya = cfma(pm, xa[j], ya);
+                yb = cfma(pm, xb[j], yb);
+            }
+            if (realbin) { ya.y = (R)0; yb.y = (R)0; }
+            // Z_k = Y_a + i Y_b; Z_{L-k} = conj(Y_a) + i conj(Y_b)
+            Z[((long)pk * MM + m) * HP + q] = cmake(ya.x - yb.y, ya.y + yb.x);
+            if (!realbin) Z[((long)pn * MM + m) * HP + q] = cmake(ya.x + yb.y, yb.x - ya.y);
+        }
+    }
+    __syncthreads();
+
+    const int nb = MM * HP;
+    const int lognb = (nb & (nb - 1)) == 0 ? 31 - __clz(nb) : -1;
+    fft_dit_inv<C, true>(Z, a.logL, nb, lognb, nb, 1, reinterpret_cast<const C*>(a.tw));
+
+    float emax = 0.f;
+    for (int idx = threadIdx.x; idx < L * nb; idx += blockDim.x) {
+        const int l = idx / nb;
+        const int rem = idx - l * nb;
+        const int m = rem >> logHP, q = rem & (HP - 1);
+        const C z = Z[idx];
+        const long nn = n0 + 2 * q;
+        const double sv = a.sinv[l];
+        double* o = a.out + ((long)l * MM + m) * N + nn;
+        const double ea = sv * (double)z.x, eb = sv * (double)z.y;
+        if (nn + 1 < N && (N & 1) == 0) {
+            if (a.accumulate) {
+                double2 v = *reinterpret_cast<double2*>(o);
+                v.x += ea;
+                v.y += eb;
+                *reinterpret_cast<double2*>(o) = v;
+            } else {
+                *reinterpret_cast<double2*>(o) = make_double2(ea, eb);
+            }
+            if (l == L - 1) emax = fmaxf(emax, fmaxf(fabsf((float)ea), fabsf((float)eb)));
+        } else {
+            if (nn < N) {
+                o[0] = a.accumulate ? o[0] + ea : ea;
+                if (l == L - 1) emax = fmaxf(emax, fabsf((float)ea));
+            }
+            if (nn + 1 < N) {
+                o[1] = a.accumulate ? o[1] + eb : eb;
+                if (l == L - 1) emax = fmaxf(emax, fabsf((float)eb));
+            }
+        }
+    }
+    const float tot = block_max(emax, red);
+    if (threadIdx.x == 0) a.part[blockIdx.x] = tot;
+}
+
+template <typename R>
+cudaError_t launch_fwd(const FwdArgs& a, int grid, size_t smem, cudaStream_t st) {
+    switch (a.M) {
+#define AC_CASE(MMV)                                                                          \
+    case MMV: {                                                                               \
+        cudaError_t e = cudaFuncSetAttribute(k_fwd<R, MMV>,                                   \
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,     \
+                                             (int)smem);                                      \
+        if (e != cudaSuccess) return e;                                                       \
+        k_fwd<R, MMV><<<grid, 256, smem, st>>>(a);                                            \
+        return cudaGetLastError();                                                            \
+    }
+        AC_CASE(1) AC_CASE(2) AC_CASE(3) AC_CASE(4)
+#undef AC_CASE
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename R>
+cudaError_t launch_upd(const UpdArgs& a, int grid, size_t smem, cudaStream_t st) {
+    switch (a.M) {
+#define AC_CASE(MMV)                                                                          \
+    case MMV: {                                                                               \
+        cudaError_t e = cudaFuncSetAttribute(k_upd<R, MMV>,                                   \
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,     \
+                                             (int)smem);                                      \
+        if (e != cudaSuccess) return e;                                                       \
+        k_upd<R, MMV><<<grid, 256, smem, st>>>(a);                                            \
+        return cudaGetLastError();                                                            \
+    }
+        AC_CASE(1) AC_CASE(2) AC_CASE(3) AC_CASE(4)
+#undef AC_CASE
+    }
+    return cudaErrorInvalidValue;
+}
+
+template cudaError_t launch_fwd<float>(const FwdArgs&, int, size_t, cudaStream_t);
+template cudaError_t launch_fwd<double>(const FwdArgs&, int, size_t, cudaStream_t);
+template cudaError_t launch_upd<float>(const UpdArgs&, int, size_t, cudaStream_t);
+template cudaError_t launch_upd<double>(const UpdArgs&, int, size_t, cudaStream_t);
+
+}  // namespace ac

@@ -1,0 +1,101 @@
+// Argument blocks and launchers of the solver kernels (internal to the
+// library).  All pointers are device pointers.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace ac {
+
+// Geometry of the periodic grid and the per-axis stencil of A.
+struct Grid {
+    int dim, nx, ny, N;      // N = nx * ny (ny = 1 in 1D)
+    int rad;                 // stencil radius (1 or 2)
+    double tx[5], ty[5];     // per-axis taps on offsets -2..2 (A = x part + y part)
+    double c0;               // tx[2] + ty[2], the combined centre tap
+};
+
+// Residual + alpha-scaling + forward time FFT + node mixing (steps i-ii and
+// eq. (d1)):  X[f][m][n] = sum_j Sinv_f[m][j] * FFT_l( s_l * (w - C u)_{l,j,n} ).
+struct FwdArgs {
+    Grid g;
+    int M, L, logL, F, P;        // P grid points per block
+    const double* u;             // L*M*N or null (then r = b)
+    const double* u0;            // N or null: block-1 right-hand side
+    const double* b;             // L*M*N or null: full right-hand side
+    int b_reversed;              // read b[L-1-l] instead of b[l]
+    int transposed;              // coupling H^T (adjoint) instead of H
+    const double* qs;            // [L][M][M] s_l * dT * Q (Q^T if transposed)
+    const double* s;             // [L] s_l = alpha^{l/L}
+    const float* inv_s_w;        // [L] 1 / (s_l * w_scale) for the residual norm
+    const void* tw;              // L/2 twiddles exp(-2 pi i k / L), complex of the kernel type
+    const void* Sinv;            // [F][M][M] complex of the kernel type
+    void* X;                     // [F][M][N] complex of the kernel type
+    float* part;                 // [gridDim.x] partial sums of (r / w_scale)^2
+};
+
+// Node back-mixing + inverse time FFT + un-scaling + update (eqs. (d3),
+// (Gsubstitution), (s3)):  out_l (+)= sinv_l * IFFT_k( P_f X[f] )_l.
+struct UpdArgs {
+    int N, M, L, logL, F, P;
+    const void* X;               // [F][M][N]
+    const void* Pm;              // [F][M][M]
+    const void* tw;              // L/2 twiddles
+    const double* sinv;          // [L] alpha^{-l/L} / L
+    double* out;                 // L*M*N
+    int accumulate;              // 1: out += e, 0: out = e
+    float* part;                 // [gridDim.x] max |e| over the last time block
+};
+
+// Spatial solves of eq. (d2) on the F*M planes X[f][m][:].
+struct SpaceArgs {
+    int nx, ny, lognx, logny, planes, M;
+    void* X;
+    const void* mu_dT;           // [F*M] complex dT * mu_{f,m}
+    const void* sig_x;           // [nx] complex symbol of the x part of A
+    const void* sig_y;           // [ny] complex symbol of the y part (2D)
+    const void* tw_x;            // nx/2 twiddles
+    const void* tw_y;            // ny/2 twiddles
+    int rows_per_block, cols_per_block;
+};
+
+// BiCGStab on (I - dT mu A) x = X-plane with the stencil, tolerance tau.
+struct BicgArgs {
+    Grid g;
+    int planes, M, max_iter;
+    double tau;
+    void* X;                     // in: right-hand sides, out: solutions
+    const void* mu_dT;
+    int* iters;                  // [planes] iterations used (negative on breakdown)
+};
+
+struct ApplyArgs {
+    Grid g;
+    int M, L, transposed;
+    const double* u;
+    double* out;
+    const double* dtQ;           // [M][M] dT * Q (Q^T if transposed)
+};
+
+struct GradArgs {
+    Grid g;
+    int M, L;
+    const double* u;
+    const double* lam;
+    const double* dtQ;           // [M][M] dT * Q
+    double d2x[5], d1x[5], d2y[5], d1y[5];  // second/first derivative taps per axis
+    double* part;                // [gridDim.x][3]
+};
+
+template <typename R> cudaError_t launch_fwd(const FwdArgs& a, int grid, size_t smem, cudaStream_t st);
+template <typename R> cudaError_t launch_upd(const UpdArgs& a, int grid, size_t smem, cudaStream_t st);
+template <typename R> cudaError_t launch_space_1d(const SpaceArgs& a, cudaStream_t st);
+template <typename R> cudaError_t launch_space_2d_small(const SpaceArgs& a, cudaStream_t st);
+template <typename R> cudaError_t launch_space_rows(const SpaceArgs& a, int inverse, cudaStream_t st);
+template <typename R> cudaError_t launch_space_cols(const SpaceArgs& a, cudaStream_t st);
+template <typename R> cudaError_t launch_bicgstab(const BicgArgs& a, cudaStream_t st);
+cudaError_t launch_apply(const ApplyArgs& a, cudaStream_t st);
+cudaError_t launch_grad(const GradArgs& a, int grid, cudaStream_t st);
+cudaError_t launch_sum_blocks(const double* lam, int M, int N, double* du0, cudaStream_t st);
+cudaError_t launch_reverse_time(double* v, int L, long long blk, cudaStream_t st);
+cudaError_t launch_norms(const double* v, long long n, double* part, int grid, cudaStream_t st);
+
+}  // namespace ac

@@ -1,0 +1,392 @@
+// Host-side planner: Radau IIA data (Sec. 2.1, 2.3), the eigen-decomposition
+// of Q G_l^{-1} per time frequency (Lemma 1, eq. (QGL), Algorithm 1), the
+// alpha sequence of Algorithm 2 and stencil symbols.
+#include "planner.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "alphacirc.h"
+
+namespace ac {
+
+// ---------------------------------------------------------------- nodes, Q
+// P_{M-1}(x) + P_M(x) and its derivative by the three-term recurrence.
+static void radau_poly(int M, double x, double* p, double* dp) {
+    double pk = 1.0, pkm1 = 0.0, dpk = 0.0, dpkm1 = 0.0;  // P_0, P_{-1}
+    double prev = 0.0, dprev = 0.0;
+    for (int k = 0; k < M; ++k) {
+        // P_{k+1} = ((2k+1) x P_k - k P_{k-1}) / (k+1)
+        double pn = ((2 * k + 1) * x * pk - k * pkm1) / (k + 1);
+        double dpn = ((2 * k + 1) * (pk + x * dpk) - k * dpkm1) / (k + 1);
+        prev = pk;
+        dprev = dpk;
+        pkm1 = pk;
+        dpkm1 = dpk;
+        pk = pn;
+        dpk = dpn;
+    }
+    *p = pk + prev;      // P_M + P_{M-1}
+    *dp = dpk + dprev;
+}
+
+bool radau_nodes(int M, double* t) {
+    if (M < 1 || M > 8) return false;
+    double x[8];
+    for (int j = 0; j < M; ++j) x[j] = -std::cos(2.0 * M_PI * j / (2.0 * M - 1.0));
+    x[0] = -1.0;
+    // Newton with deflation of the roots already found
+    for (int j = 1; j < M; ++j) {
+        double xj = x[j];
+        for (int it = 0; it < 100; ++it) {
+            double p, dp;
+            radau_poly(M, xj, &p, &dp);
+            double s = 0.0;
+            for (int i = 0; i < j; ++i) s += 1.0 / (xj - x[i]);
+            double step = p / (dp - p * s);
+            xj -= step;
+            if (std::fabs(step) < 1e-17) break;
+        }
+        x[j] = xj;
+    }
+    for (int j = 0; j < M; ++j) t[j] = 0.5 * (1.0 - x[j]);
+    std::sort(t, t + M);
+    t[M - 1] = 1.0;
+    return true;
+}
+
+// Dense real solve A X = B (n x n, nrhs columns) by Gaussian elimination with
+// partial pivoting; A, B row-major, overwritten.
+static bool solve_real(int n, double* A, int nrhs, double* B) {
+    for (int c = 0; c < n; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < n; ++r)
+            if (std::fabs(A[r * n + c]) > std::fabs(A[piv * n + c])) piv = r;
+        if (A[piv * n + c] == 0.0) return false;
+        if (piv != c) {
+            for (int k = 0; k < n; ++k) std::swap(A[c * n + k], A[piv * n + k]);
+            for (int k = 0; k < nrhs; ++k) std::swap(B[c * nrhs + k], B[piv * nrhs + k]);
+        }
+        for (int r = c + 1; r < n; ++r) {
+            double f = A[r * n + c] / A[c * n + c];
+            for (int k = c; k < n; ++k) A[r * n + k] -= f * A[c * n + k];
+            for (int k = 0; k < nrhs; ++k) B[r * nrhs + k] -= f * B[c * nrhs + k];
+        }
+    }
+    for (int c = n - 1; c >= 0; --c)
+        for (int k = 0; k < nrhs; ++k) {
+            double s = B[c * nrhs + k];
+            for (int j = c + 1; j < n; ++j) s -= A[c * n + j] * B[j * nrhs + k];
+            B[c * nrhs + k] = s / A[c * n + c];
+        }
+    return true;
+}
+
+// Q maps the monomials t^k to t^{k+1}/(k+1) on the nodes (the Vandermonde
+// relation Q W = D_M W of Lemma 2's proof), so Q = W' W^{-1}; solved here as
+// W^T Q^T = W'^T.
+bool collocation_matrix(int M, const double* t, double* Q) {
+    if (M < 1 || M > 8) return false;
+    double WT[64], WpT[64];
+    for (int m = 0; m < M; ++m)
+        for (int k = 0; k < M; ++k) {
+            WT[k * M + m] = std::pow(t[m], k);
+            WpT[k * M + m] = std::pow(t[m], k + 1) / (k + 1);
+        }
+    if (!solve_real(M, WT, M, WpT)) return false;  // WpT now holds Q^T
+    for (int m = 0; m < M; ++m)
+        for (int i = 0; i < M; ++i) Q[m * M + i] = WpT[i * M + m];
+    return true;
+}
+
+// ------------------------------------------------------- small complex eig
+// Complex Schur form by Householder reduction to Hessenberg form and shifted
+// QR steps with Givens rotations; eigenvectors by back substitution.
+static bool schur_small(int n, cd* A, cd* Z) {
+    for (int i = 0; i < n * n; ++i) Z[i] = 0.0;
+    for (int i = 0; i < n; ++i) Z[i * n + i] = 1.0;
+    // Hessenberg reduction
+    for (int k = 0; k + 2 < n; ++k) {
+        int len = n - k - 1;
+        cd v[8];
+        double xn = 0.0;
+        for (int i = 0; i < len; ++i) {
+            v[i] = A[(k + 1 + i) * n + k];
+            xn += std::norm(v[i]);
+        }
+        xn = std::sqrt(xn);
+        if (xn == 0.0) continue;
+        cd ph = std::abs(v[0]) > 0 ? v[0] / std::abs(v[0]) : cd(1.0);
+        v[0] += ph * xn;
+        double vn = 0.0;
+        for (int i = 0; i < len; ++i) vn += std::norm(v[i]);
+        vn = std::sqrt(vn);
+        for (int i = 0; i < len; ++i) v[i] /= vn;
+        // A <- (I - 2 v v^H) A (rows k+1..)
+        for (int j = 0; j < n; ++j) {
+            cd s = 0.0;
+            for (int i = 0; i < len; ++i) s += std::conj(v[i]) * A[(k + 1 + i) * n + j];
+            for (int i = 0; i < len; ++i) A[(k + 1 + i) * n + j] -= 2.0 * v[i] * s;
+        }
+        // A <- A (I - 2 v v^H) (cols k+1..), Z likewise
+        for (int r = 0; r < n; ++r) {
+            cd s = 0.0, sz = 0.0;
+            for (int i = 0; i < len; ++i) {
+                s += A[r * n + k + 1 + i] * v[i];
+                sz += Z[r * n + k + 1 + i] * v[i];
+            }
+            for (int i = 0; i < len; ++i) {
+                A[r * n + k + 1 + i] -= 2.0 * s * std::conj(v[i]);
+                Z[r * n + k + 1 + i] -= 2.0 * sz * std::conj(v[i]);
+            }
+        }
+        for (int i = k + 2; i < n; ++i) A[i * n + k] = 0.0;
+    }
+    // shifted QR iterations
+    const double eps = 2.220446049250313e-16;
+    int hi = n - 1, iter = 0, total = 0;
+    while (hi > 0) {
+        if (++total > 1000) return false;
+        int l = hi;
+        while (l > 0) {
+            double s = std::abs(A[l * n + l]) + std::abs(A[(l - 1) * n + l - 1]);
+            if (std::abs(A[l * n + l - 1]) <= eps * (s > 0 ? s : 1.0)) break;
+            --l;
+        }
+        if (l > 0) A[l * n + l - 1] = 0.0;
+        if (l == hi) {
+            --hi;
+            iter = 0;
+            continue;
+        }
+        ++iter;
+        // Wilkinson shift from the trailing 2x2 block
+        cd a = A[(hi - 1) * n + hi - 1], b = A[(hi - 1) * n + hi];
+        cd c = A[hi * n + hi - 1], d = A[hi * n + hi];
+        cd tr2 = 0.5 * (a + d);
+        cd disc = std::sqrt(0.25 * (a - d) * (a - d) + b * c);
+        cd mu1 = tr2 + disc, mu2 = tr2 - disc;
+        cd mu = std::abs(mu1 - d) < std::abs(mu2 - d) ? mu1 : mu2;
+        if (iter % 11 == 10) mu = d + cd(std::abs(c), 0.0);  // exceptional shift
+        for (int k = l; k <= hi; ++k) A[k * n + k] -= mu;
+        cd gc[8], gs[8];
+        for (int k = l; k < hi; ++k) {
+            cd x = A[k * n + k], y = A[(k + 1) * n + k];
+            double r = std::sqrt(std::norm(x) + std::norm(y));
+            cd cc = r > 0 ? x / r : cd(1.0), ss = r > 0 ? y / r : cd(0.0);
+            gc[k] = cc;
+            gs[k] = ss;
+            for (int j = k; j < n; ++j) {  // rows k, k+1 <- G [row k; row k+1]
+                cd p = A[k * n + j], q = A[(k + 1) * n + j];
+                A[k * n + j] = std::conj(cc) * p + std::conj(ss) * q;
+                A[(k + 1) * n + j] = -ss * p + cc * q;
+            }
+        }
+        for (int k = l; k < hi; ++k) {  // columns k, k+1 <- [col k, col k+1] G^H
+            cd cc = gc[k], ss = gs[k];
+            int rmax = std::min(k + 2, n - 1);
+            for (int r = 0; r <= rmax; ++r) {
+                cd p = A[r * n + k], q = A[r * n + k + 1];
+                A[r * n + k] = p * cc + q * ss;
+                A[r * n + k + 1] = -p * std::conj(ss) + q * std::conj(cc);
+            }
+            for (int r = 0; r < n; ++r) {
+                cd p = Z[r * n + k], q = Z[r * n + k + 1];
+                Z[r * n + k] = p * cc + q * ss;
+                Z[r * n + k + 1] = -p * std::conj(ss) + q * std::conj(cc);
+            }
+        }
+        for (int k = l; k <= hi; ++k) A[k * n + k] += mu;
+    }
+    return true;
+}
+
+// Inverse by Gauss-Jordan with partial pivoting; returns false if singular.
+static bool invert_small(int n, const cd* S, cd* X) {
+    cd a[64];
+    std::memcpy(a, S, sizeof(cd) * n * n);
+    for (int i = 0; i < n * n; ++i) X[i] = 0.0;
+    for (int i = 0; i < n; ++i) X[i * n + i] = 1.0;
+    for (int c = 0; c < n; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < n; ++r)
+            if (std::abs(a[r * n + c]) > std::abs(a[piv * n + c])) piv = r;
+        if (std::abs(a[piv * n + c]) == 0.0) return false;
+        if (piv != c)
+            for (int k = 0; k < n; ++k) {
+                std::swap(a[c * n + k], a[piv * n + k]);
+                std::swap(X[c * n + k], X[piv * n + k]);
+            }
+        cd inv = 1.0 / a[c * n + c];
+        for (int k = 0; k < n; ++k) {
+            a[c * n + k] *= inv;
+            X[c * n + k] *= inv;
+        }
+        for (int r = 0; r < n; ++r) {
+            if (r == c) continue;
+            cd f = a[r * n + c];
+            if (f == 0.0) continue;
+            for (int k = 0; k < n; ++k) {
+                a[r * n + k] -= f * a[c * n + k];
+                X[r * n + k] -= f * X[c * n + k];
+            }
+        }
+    }
+    return true;
+}
+
+static double norm1(int n, const cd* A) {
+    double best = 0.0;
+    for (int j = 0; j < n; ++j) {
+        double s = 0.0;
+        for (int i = 0; i < n; ++i) s += std::abs(A[i * n + j]);
+        best = std::max(best, s);
+    }
+    return best;
+}
+
+double eig_small(int n, const cd* B, cd* mu, cd* S, cd* Sinv) {
+    cd T[64], Z[64];
+    std::memcpy(T, B, sizeof(cd) * n * n);
+    if (!schur_small(n, T, Z)) return -1.0;
+    double scale = norm1(n, B);
+    if (scale == 0.0) scale = 1.0;
+    for (int k = 0; k < n; ++k) {
+        mu[k] = T[k * n + k];
+        cd y[8];
+        for (int i = 0; i < n; ++i) y[i] = 0.0;
+        y[k] = 1.0;
+        for (int i = k - 1; i >= 0; --i) {
+            cd s = 0.0;
+            for (int j = i + 1; j <= k; ++j) s += T[i * n + j] * y[j];
+            cd den = T[i * n + i] - T[k * n + k];
+            if (std::abs(den) < 1e-14 * scale) den = cd(1e-14 * scale, 0.0);  // defective: cond(S) will expose it
+            y[i] = -s / den;
+        }
+        double nrm = 0.0;
+        cd v[8];
+        for (int r = 0; r < n; ++r) {
+            v[r] = 0.0;
+            for (int j = 0; j <= k; ++j) v[r] += Z[r * n + j] * y[j];
+            nrm += std::norm(v[r]);
+        }
+        nrm = std::sqrt(nrm);
+        for (int r = 0; r < n; ++r) S[r * n + k] = v[r] / nrm;
+    }
+    if (!invert_small(n, S, Sinv)) return 1e300;
+    return norm1(n, S) * norm1(n, Sinv);
+}
+
+double freq_tables(int M, int L, double alpha, bool transposed, const double* Q,
+                   const double* t, cd* mu, cd* Sinv, cd* P, double* cond) {
+    (void)t;
+    const int F = L / 2 + 1;
+    double worst = 0.0;
+    for (int f = 0; f < F; ++f) {
+        // d_f of Lemma 1 (0-based f), r_f = d_f / (1 + d_f)
+        cd d = -std::pow(alpha, 1.0 / L) * std::exp(cd(0.0, -2.0 * M_PI * f / L));
+        cd r = d / (1.0 + d);
+        // G_f^{-1} = I - r H_M  (H_M^T for the transposed system)
+        cd Ginv[64], B[64], S[64];
+        for (int i = 0; i < M; ++i)
+            for (int j = 0; j < M; ++j) {
+                double h = transposed ? (i == M - 1 ? 1.0 : 0.0) : (j == M - 1 ? 1.0 : 0.0);
+                Ginv[i * M + j] = (i == j ? 1.0 : 0.0) - r * h;
+            }
+        for (int i = 0; i < M; ++i)
+            for (int j = 0; j < M; ++j) {
+                cd s = 0.0;
+                for (int k = 0; k < M; ++k)
+                    s += (transposed ? Q[k * M + i] : Q[i * M + k]) * Ginv[k * M + j];
+                B[i * M + j] = s;
+            }
+        double c = eig_small(M, B, mu + f * M, S, Sinv + f * M * M);
+        if (c < 0) return -1.0;
+        if (cond) cond[f] = c;
+        worst = std::max(worst, c);
+        for (int i = 0; i < M; ++i)
+            for (int j = 0; j < M; ++j) {
+                cd s = 0.0;
+                for (int k = 0; k < M; ++k) s += Ginv[i * M + k] * S[k * M + j];
+                P[(f * M + i) * M + j] = s;
+            }
+    }
+    return worst;
+}
+
+// ---------------------------------------------------------------- stencils
+void central_coeffs(int order, double d1[5], double d2[5]) {
+    for (int i = 0; i < 5; ++i) d1[i] = d2[i] = 0.0;
+    if (order == 4) {
+        d1[0] = 1.0 / 12; d1[1] = -8.0 / 12; d1[3] = 8.0 / 12; d1[4] = -1.0 / 12;
+        d2[0] = -1.0 / 12; d2[1] = 16.0 / 12; d2[2] = -30.0 / 12; d2[3] = 16.0 / 12; d2[4] = -1.0 / 12;
+    } else {
+        d1[1] = -0.5; d1[3] = 0.5;
+        d2[1] = 1.0; d2[2] = -2.0; d2[3] = 1.0;
+    }
+}
+
+void axis_taps(int order, int n, double length, double nu, double c, double taps[5]) {
+    double d1[5], d2[5];
+    central_coeffs(order, d1, d2);
+    double h = length / n;
+    for (int i = 0; i < 5; ++i) taps[i] = nu * d2[i] / (h * h) - c * d1[i] / h;
+}
+
+void axis_symbol(int n, const double taps[5], cd* sigma) {
+    for (int k = 0; k < n; ++k) {
+        cd s = 0.0;
+        for (int o = -2; o <= 2; ++o) {
+            if (taps[o + 2] == 0.0) continue;
+            long long ko = ((long long)k * (o + n)) % n;  // k*o mod n, nonnegative
+            double th = 2.0 * M_PI * (double)ko / n;
+            s += taps[o + 2] * cd(std::cos(th), std::sin(th));
+        }
+        sigma[k] = s;
+    }
+}
+
+}  // namespace ac
+
+// ------------------------------------------------------------- C ABI (host)
+extern "C" int ac_radau_nodes(int M, double* t) {
+    if (!t) return AC_ERR_INVALID_ARG;
+    return ac::radau_nodes(M, t) ? AC_OK : AC_ERR_INVALID_ARG;
+}
+
+extern "C" int ac_collocation_matrix(int M, double* Q) {
+    double t[8];
+    if (!Q || !ac::radau_nodes(M, t)) return AC_ERR_INVALID_ARG;
+    return ac::collocation_matrix(M, t, Q) ? AC_OK : AC_ERR_INVALID_ARG;
+}
+
+extern "C" int ac_freq_tables(int M, int L, double alpha, int transposed, double* mu,
+                              double* Sinv, double* P, double* cond) {
+    if (M < 1 || M > 8 || L < 1 || !(alpha > 0.0) || !(alpha < 1.0) || !mu || !Sinv || !P)
+        return AC_ERR_INVALID_ARG;
+    double t[8], Q[64];
+    ac::radau_nodes(M, t);
+    ac::collocation_matrix(M, t, Q);
+    const int F = L / 2 + 1;
+    std::vector<ac::cd> vmu(F * M), vS(F * M * M), vP(F * M * M);
+    double worst = ac::freq_tables(M, L, alpha, transposed != 0, Q, t, vmu.data(), vS.data(),
+                                   vP.data(), cond);
+    std::memcpy(mu, vmu.data(), sizeof(double) * 2 * F * M);
+    std::memcpy(Sinv, vS.data(), sizeof(double) * 2 * F * M * M);
+    std::memcpy(P, vP.data(), sizeof(double) * 2 * F * M * M);
+    if (worst < 0 || worst > 1e10) return AC_ERR_NOT_DIAGONALIZABLE;
+    return AC_OK;
+}
+
+extern "C" int ac_alpha_sequence(double m0, double gamma, int n, double* alphas, double* ms) {
+    if (!(m0 > 0) || !(gamma > 0) || n < 0 || !alphas || !ms) return AC_ERR_INVALID_ARG;
+    double m = m0;
+    ms[0] = m0;
+    for (int k = 0; k < n; ++k) {
+        alphas[k] = std::sqrt(gamma / m);   // alpha_{k+1} = sqrt(gamma / m_k)
+        m = 2.0 * std::sqrt(m * gamma);     // m_{k+1} = 2 sqrt(m_k gamma)
+        ms[k + 1] = m;
+    }
+    return AC_OK;
+}

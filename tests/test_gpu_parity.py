@@ -1,0 +1,168 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle."""
+import math
+
+import numpy as np
+import pytest
+
+from gpu_common import oracle_setup, rel2, to_dev, torch_cuda
+from oracle import fourier, operators, paradiag, sequential
+from paper_2103_12571_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+EPS64 = 2.0 ** -53
+EPS32 = 2.0 ** -24
+
+# small problems spanning several tiles, both dimensions, both orders, M = 1..4
+SMALL = [
+    workloads.problem(1, 64, nu=0.1, order=2, M=2, L=4, T=0.1),
+    workloads.problem(1, 8, nu=0.3, cx=0.7, order=2, M=1, L=2, T=0.1),
+    workloads.problem(1, 512, cx=1.0, order=4, M=3, L=16, T=0.25),
+    workloads.problem(1, 256, nu=0.01, cx=-0.5, order=4, M=4, L=8, T=0.1),
+    workloads.problem(2, 32, 16, nu=0.05, order=2, M=3, L=8, T=0.1),
+    workloads.problem(2, 64, 64, nu=1e-3, cx=1.0, cy=0.5, order=2, M=3, L=32, T=0.25),
+    workloads.problem(2, 16, 32, nu=0.02, cx=0.3, cy=-0.2, order=4, M=2, L=4, T=0.05),
+    workloads.problem(2, 128, 256, nu=0.05, order=2, M=3, L=8, T=0.0625),   # three-pass 2D path
+]
+
+
+def ids(p):
+    return "d%d_%dx%d_o%d_M%d_L%d" % (p["dim"], p["nx"], p["ny"], p["order"], p["M"], p["L"])
+
+
+def rand_field(rng, prob):
+    N = operators.n_points(prob)
+    return rng.standard_normal((prob["L"], prob["M"], N))
+
+
+@pytest.mark.parametrize("prob", SMALL, ids=ids)
+def test_apply_C_and_CT(prob):
+    torch = torch_cuda()
+    from paper_2103_12571_gb300.api import Plan
+    Q, A, dT = oracle_setup(prob)
+    rng = np.random.default_rng(0)
+    u = rand_field(rng, prob)
+    plan = Plan(prob)
+    Cu = plan.apply_C(to_dev(torch, u)).cpu().numpy()
+    ref = operators.apply_C(u, A, Q, dT)
+    assert rel2(Cu, ref) < 1e-14
+    CTu = plan.apply_CT(to_dev(torch, u)).cpu().numpy()
+    assert rel2(CTu, operators.apply_CT(u, A, Q, dT)) < 1e-14
+
+
+@pytest.mark.parametrize("prob", SMALL, ids=ids)
+@pytest.mark.parametrize("precision", ["c128", "c64"])
+def test_precond_solve(prob, precision):
+    """e = C_alpha^{-1} r against the oracle's Lemma-1 route with sparse block
+    solves.  Tolerance from Theorem 2: the error is bounded by a modest
+    multiple of L (3 eps + tau) / alpha relative to the data."""
+    torch = torch_cuda()
+    from paper_2103_12571_gb300.api import Plan
+    Q, A, dT = oracle_setup(prob)
+    rng = np.random.default_rng(1)
+    r = rand_field(rng, prob)
+    plan = Plan(prob, precision=precision)
+    L = prob["L"]
+    eps = EPS64 if precision == "c128" else EPS32
+    for alpha in (1e-2, 1e-4):
+        e = plan.precond_solve(alpha, to_dev(torch, r)).cpu().numpy()
+        ref = paradiag.precond_solve(A, Q, dT, alpha, r).real
+        tol = 20 * L * 3 * eps / alpha
+        assert rel2(e, ref) < tol, (alpha, rel2(e, ref), tol)
+
+
+@pytest.mark.parametrize("prob", SMALL, ids=ids)
+@pytest.mark.parametrize("precision,alpha_mode,tol", [("c128", "paper", 1e-11), ("c64", "mixed", 1e-10)])
+def test_richardson_solve_matches_sequential_oracle(prob, precision, alpha_mode, tol):
+    torch = torch_cuda()
+    from paper_2103_12571_gb300.api import Plan
+    Q, A, dT = oracle_setup(prob)
+    rng = np.random.default_rng(2)
+    N = operators.n_points(prob)
+    u0 = rng.standard_normal(N)
+    ref = sequential.sequential_solve(A, Q, dT, prob["L"], u0)
+    plan = Plan(prob, precision=precision, alpha=alpha_mode, max_iter=40)
+    u, st = plan.solve(to_dev(torch, u0), tol=1e-14 if precision == "c128" else 1e-13, raise_on_fail=False)
+    err = rel2(u.cpu().numpy(), ref)
+    assert err < tol, (err, st)
+    # the residual the library reports is the true one of the returned iterate,
+    # up to the rounding noise of evaluating w - C u in FP64 (about
+    # eps (1 + dT ||A||_inf) ||u|| / ||w|| per entry)
+    uh = u.cpu().numpy()
+    Cu = operators.apply_C(uh, A, Q, dT)
+    w = operators.rhs_w(u0, prob["L"], prob["M"])
+    floor = 64 * EPS64 * (1 + dT * abs(A).sum(axis=1).max()) * np.linalg.norm(uh) / np.linalg.norm(w)
+    assert abs(np.linalg.norm(w - Cu) / np.linalg.norm(w) - st["res_rel"][-1]) < 1e-3 * st["res_rel"][-1] + floor
+
+
+def test_config1_fixed_alpha_against_closed_form():
+    torch = torch_cuda()
+    from paper_2103_12571_gb300.api import Plan
+    prob, u0, ex = workloads.config(1)
+    Q, A, dT = oracle_setup(prob)
+    ref = fourier.modal_solution(u0, prob, Q, dT, prob["L"])
+    plan = Plan(prob, precision="c128", alpha="fixed", alpha0=ex["alpha"], max_iter=20)
+    u, st = plan.solve(to_dev(torch, u0), tol=ex["tol"])
+    assert st["converged"]
+    assert rel2(u.cpu().numpy(), ref) < 1e-11
+    # each iteration contracts the error by about alpha (Theorem 1)
+    assert st["iters"] <= 5
+
+
+def test_richardson_contraction_matches_closed_form_per_mode():
+    """With one Fourier mode, each GPU iteration multiplies the last-node
+    error by -alpha R^L / (1 - alpha R^L) (derived from eqs. (prec),
+    (Riteration)); checked on the FP64 path."""
+    torch = torch_cuda()
+    from paper_2103_12571_gb300.api import Plan
+    prob = workloads.problem(1, 32, nu=0.2, M=3, L=8, T=0.4)
+    Q, A, dT = oracle_setup(prob)
+    k = 3
+    u0 = np.cos(2 * np.pi * k * np.arange(32) / 32)
+    ustar = sequential.sequential_solve(A, Q, dT, 8, u0)
+    alpha = 0.05
+    plan = Plan(prob, precision="c128")
+    u = to_dev(torch, np.broadcast_to(u0, (8, 3, 32)).copy())
+    d0 = to_dev(torch, u0)
+    errs = []
+    for _ in range(5):
+        errs.append(u.cpu().numpy()[-1, -1] - ustar[-1, -1])
+        plan.richardson_step(alpha, d0, u)
+    fac = fourier.contraction_factor(np.array([dT * fourier.symbol(prob)[k]]), alpha, 8, Q)[0].real
+    for a, b in zip(errs[:-1], errs[1:]):
+        if np.max(np.abs(a)) > 1e-10:
+            np.testing.assert_allclose(b, fac * a, atol=1e-13 + 1e-8 * np.max(np.abs(a)))
+
+
+def test_zero_rhs_gives_zero():
+    torch = torch_cuda()
+    from paper_2103_12571_gb300.api import Plan
+    prob = workloads.problem(1, 64, nu=0.1, M=2, L=4, T=0.1)
+    plan = Plan(prob)
+    u, st = plan.solve(torch.zeros(64, dtype=torch.float64, device="cuda"), tol=1e-12)
+    assert st["converged"] and float(u.abs().max()) == 0.0
+
+
+@pytest.mark.parametrize("prob", [SMALL[2], SMALL[5], SMALL[6]], ids=ids)
+@pytest.mark.parametrize("precision", ["c128", "c64"])
+def test_adjoint_and_gradients(prob, precision):
+    torch = torch_cuda()
+    from paper_2103_12571_gb300.api import Plan
+    Q, A, dT = oracle_setup(prob)
+    rng = np.random.default_rng(3)
+    N = operators.n_points(prob)
+    g = rng.standard_normal((prob["L"], prob["M"], N))
+    lam_ref = sequential.sequential_adjoint(A, Q, dT, g)
+    plan = Plan(prob, precision=precision, alpha="paper" if precision == "c128" else "mixed", max_iter=40)
+    lam, st = plan.adjoint_solve(to_dev(torch, g), tol=1e-14 if precision == "c128" else 1e-13,
+                                 raise_on_fail=False)
+    lam = lam.cpu().numpy()
+    assert rel2(lam, lam_ref) < (1e-11 if precision == "c128" else 1e-10), st
+    u0 = rng.standard_normal(N)
+    u = sequential.sequential_solve(A, Q, dT, prob["L"], u0)
+    du0, dp = plan.grad_params(to_dev(torch, u), to_dev(torch, lam))
+    du0_ref, dnu_ref, dc_ref = sequential.grad_params(prob, Q, dT, u, lam_ref)
+    assert rel2(du0.cpu().numpy(), du0_ref) < 1e-9
+    ref = np.array([dnu_ref, dc_ref[0], dc_ref[1]])
+    for i in range(3):
+        assert abs(dp[i] - ref[i]) <= 1e-9 * max(1.0, np.max(np.abs(ref))), (i, dp, ref)

@@ -1,0 +1,103 @@
+"""The C ABI library on the CPU: it builds, loads, exports every declared
+symbol, and its host-side planner agrees with the oracle (no GPU calls)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from conftest import ROOT
+from oracle import alpha_rule, collocation, paradiag
+
+
+@pytest.fixture(scope="module")
+def api():
+    from paper_2103_12571_gb300 import build
+    build.build()
+    from paper_2103_12571_gb300 import api as A
+    return A
+
+
+def declared_symbols():
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for f in os.listdir(inc):
+        if f.endswith(".h"):
+            txt = open(os.path.join(inc, f)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(ac_[a-z_0-9]+)\s*\(", txt))
+    return sorted(names)
+
+
+def test_library_exports_every_declared_symbol(api):
+    from paper_2103_12571_gb300 import _lib
+    L = ctypes.CDLL(_lib.LIB_PATH)
+    syms = declared_symbols()
+    assert len(syms) >= 15
+    for s in syms:
+        assert hasattr(L, s), s
+
+
+@pytest.mark.parametrize("M", [1, 2, 3, 4, 5, 6])
+def test_host_nodes_and_Q_match_oracle(api, M):
+    t = collocation.radau_iia_nodes(M)
+    np.testing.assert_allclose(api.radau_nodes(M), t, atol=2e-15)
+    np.testing.assert_allclose(api.collocation_matrix(M), collocation.collocation_matrix(t), atol=5e-14)
+
+
+@pytest.mark.parametrize("M,L,alpha", [(2, 4, 1e-4), (3, 64, 3e-3), (3, 512, 1e-2), (4, 16, 0.3), (1, 8, 1e-6)])
+@pytest.mark.parametrize("transposed", [False, True])
+def test_host_eigen_tables(api, M, L, alpha, transposed):
+    rc, mu, Sinv, P, cond = api.freq_tables(M, L, alpha, transposed)
+    assert rc == 0
+    t = collocation.radau_iia_nodes(M)
+    Q = collocation.collocation_matrix(t)
+    H = collocation.H_matrix(M)
+    d = paradiag.eigenvalues_d(L, alpha)
+    for f in range(L // 2 + 1):
+        r = d[f] / (1 + d[f])
+        Hm = H.T if transposed else H
+        Ginv = np.eye(M) - r * Hm
+        B = (Q.T if transposed else Q) @ Ginv
+        S = np.linalg.inv(Sinv[f])
+        np.testing.assert_allclose(B @ S, S @ np.diag(mu[f]), atol=1e-12 * cond[f])
+        np.testing.assert_allclose(P[f], Ginv @ S, atol=1e-12 * cond[f])
+        # eigenvalues against Lemma 2 / numpy
+        if not transposed:
+            ev = list(np.roots(paradiag.lemma2_char_poly(t, r)[::-1]))
+            for x in mu[f]:
+                j = int(np.argmin([abs(x - e) for e in ev]))
+                assert abs(x - ev.pop(j)) < 1e-10
+        assert cond[f] < 1e6
+
+
+def test_host_eigen_guard_on_defective_block(api):
+    # M = 2: Q G^{-1} is defective where 9 r^2 - 6 r - 2 = 0, r = (1 - sqrt 3)/3,
+    # i.e. d = r / (1 - r); with L = 2 the f = 0 block has d = -alpha^{1/2}
+    r = (1 - 3 ** 0.5) / 3
+    d = r / (1 - r)
+    alpha = d * d
+    rc, mu, Sinv, P, cond = api.freq_tables(2, 2, alpha, False)
+    assert rc == -2 and cond[0] > 1e10 or cond[0] > 1e6
+    rc2, *_ = api.freq_tables(2, 2, alpha * 1.5, False)
+    assert rc2 == 0
+
+
+def test_host_alpha_sequence_matches_oracle(api):
+    a, m = api.alpha_sequence(2e-3, 7.66e-16, 6)
+    ao, mo = alpha_rule.alpha_sequence(2e-3, 7.66e-16, kmax=6)
+    np.testing.assert_allclose(a, ao, rtol=1e-15)
+    np.testing.assert_allclose(m, mo, rtol=1e-15)
+
+
+def test_setup_rejects_bad_arguments(api):
+    from paper_2103_12571_gb300 import workloads
+    from paper_2103_12571_gb300._lib import ACError
+    p = workloads.problem(1, 64, nu=0.1, M=2, L=4, T=0.1)
+    for kw in (dict(L=6), dict(M=0), dict(M=5), dict(L=1), dict(dT=-1.0)):
+        with pytest.raises(ACError) as e:
+            api.Plan(p, **kw)
+        assert e.value.code == -1
+    with pytest.raises(ACError):
+        api.Plan(workloads.problem(1, 48, nu=0.1, M=2, L=4), inner="fft")
