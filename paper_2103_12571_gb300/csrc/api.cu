@@ -177,10 +177,11 @@ static cudaError_t upload_c(const ac_plan* p, void* dst, const cd* src, size_t n
     return cudaMemcpyAsync(dst, tmp.data(), tmp.size() * sizeof(float), cudaMemcpyHostToDevice, st);
 }
 
+// w_n^k = exp(-2 pi i k / n), k < n (the full circle: the mixed-radix
+// stages index it with j * r)
 static void twiddles(int n, std::vector<cd>& tw) {
-    tw.resize(std::max(1, n / 2));
-    for (int k = 0; k < n / 2; ++k) tw[k] = std::exp(cd(0.0, -2.0 * M_PI * k / n));
-    if (n / 2 == 0) tw[0] = 1.0;
+    tw.resize(n);
+    for (int k = 0; k < n; ++k) tw[k] = std::exp(cd(0.0, -2.0 * M_PI * k / n));
 }
 
 // Alpha-dependent tables: qs, s, inv_s_w, sinv (FP64/FP32) and the per-frequency
@@ -592,7 +593,7 @@ int ac_setup(const ac_problem* prob, int M, int L, double dT, const ac_alpha_sch
     // tile of the time kernels: P points, L*M*P reals of shared memory
     const size_t rsz = cs / 2;
     int P = 256;
-    while (P > 2 && (size_t)L * M * P * rsz > 100 * 1024) P >>= 1;
+    while (P > 2 && (size_t)L * M * P * rsz > 50 * 1024) P >>= 1;
     while (P > 16 && (p->N + P - 1) / P < 2 * 152) P >>= 1;
     if ((size_t)L * M * P * rsz > 200 * 1024) {
         ac_destroy(p);
@@ -609,9 +610,9 @@ int ac_setup(const ac_problem* prob, int M, int L, double dT, const ac_alpha_sch
     } while (0)
     const int F = p->F;
     AL(p->X, (size_t)F * M * p->N * cs);
-    AL(p->tw_L, (size_t)std::max(1, L / 2) * cs);
-    AL(p->tw_x, (size_t)std::max(1, prob->nx / 2) * cs);
-    AL(p->tw_y, (size_t)std::max(1, ny / 2) * cs);
+    AL(p->tw_L, (size_t)L * cs);
+    AL(p->tw_x, (size_t)prob->nx * cs);
+    AL(p->tw_y, (size_t)ny * cs);
     AL(p->sig_x, (size_t)prob->nx * cs);
     AL(p->sig_y, (size_t)ny * cs);
     AL(p->sigT_x, (size_t)prob->nx * cs);

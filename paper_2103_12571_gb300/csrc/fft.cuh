@@ -1,0 +1,231 @@
+// Mixed-radix (8, 4, 2) in-place FFTs over batches of columns held in shared
+// memory, for power-of-two lengths, plus FP64 <-> FP32 conversions on the
+// integer pipe.
+//
+// Forward transforms are decimation in frequency: natural order in,
+// "digit-reversed" order out; inverse transforms are decimation in time from
+// that order back to natural order.  The solver only needs to know which slot
+// holds which frequency (digitrev), so no reordering pass is ever made.
+//
+// A DIF stage of radix R on blocks of size ns (m = ns / R) maps, for every
+// j < m, the R inputs x_q = data[j + q m] to
+//     y_r = w_ns^{j r} sum_q x_q w_R^{q r},   w_n = exp(-2 pi i / n),
+// stored at data[j + r m]; the inverse stage undoes it (up to a factor R).
+#pragma once
+#include "common.cuh"
+
+namespace ac {
+
+// stage plan: radix 8 while at least 3 bits remain, then one radix 4 or 2
+__host__ __device__ __forceinline__ int fft_nstages(int logn) { return (logn + 2) / 3; }
+__host__ __device__ __forceinline__ int fft_stage_bits(int logn, int s) {
+    const int full = logn / 3;
+    return s < full ? 3 : logn - 3 * full;
+}
+
+// slot of frequency k after the forward transform (and input slot of the inverse)
+__host__ __device__ __forceinline__ int digitrev(int k, int logn) {
+    int p = 0, used = 0;
+    const int ns = fft_nstages(logn);
+    for (int s = 0; s < ns; ++s) {
+        const int b = fft_stage_bits(logn, s);
+        used += b;
+        p |= (k & ((1 << b) - 1)) << (logn - used);
+        k >>= b;
+    }
+    return p;
+}
+
+// frequency held by slot p (inverse of digitrev)
+__host__ __device__ __forceinline__ int slot_freq(int p, int logn) {
+    int k = 0, used = 0, shift = 0;
+    const int ns = fft_nstages(logn);
+    for (int s = 0; s < ns; ++s) {
+        const int b = fft_stage_bits(logn, s);
+        used += b;
+        k |= ((p >> (logn - used)) & ((1 << b) - 1)) << shift;
+        shift += b;
+    }
+    return k;
+}
+
+// cos(2 pi k / 16) for k < 16, as a literal of the working precision, used
+// by the register DFTs (k is a compile-time constant after unrolling)
+template <typename R>
+__device__ __forceinline__ R cos16(int k) {
+    switch (k & 15) {
+        case 0: return (R)1.0;
+        case 1: case 15: return (R)0.92387953251128675613;
+        case 2: case 14: return (R)0.70710678118654752440;
+        case 3: case 13: return (R)0.38268343236508977173;
+        case 4: case 12: return (R)0.0;
+        case 5: case 11: return (R)-0.38268343236508977173;
+        case 6: case 10: return (R)-0.70710678118654752440;
+        case 7: case 9: return (R)-0.92387953251128675613;
+        default: return (R)-1.0;
+    }
+}
+
+template <typename C, bool INV>
+__device__ __forceinline__ C rot(C a, int k, int n) {
+    // a * exp(-+2 pi i k / n), n in {2, 4, 8, 16}
+    typedef decltype(a.x) R;
+    if (k == 0) return a;
+    const int kk = k * (16 / n);
+    const R c = cos16<R>(kk);
+    const R s = INV ? cos16<R>(kk + 12) : -cos16<R>(kk + 12);   // -+ sin(2 pi kk / 16)
+    C r;
+    r.x = a.x * c - a.y * s;
+    r.y = a.x * s + a.y * c;
+    return r;
+}
+
+// In-register R-point DFT (forward: y_r = sum_q x_q w_R^{qr}; INV: conjugate),
+// natural order in and out.
+template <int R, bool INV, typename C>
+__device__ __forceinline__ void small_dft(C* v) {
+#pragma unroll
+    for (int h = R / 2; h >= 1; h >>= 1) {
+#pragma unroll
+        for (int j0 = 0; j0 < R; j0 += 2 * h) {
+#pragma unroll
+            for (int k = 0; k < h; ++k) {
+                C a = v[j0 + k], b = v[j0 + k + h];
+                v[j0 + k] = cadd(a, b);
+                v[j0 + k + h] = rot<C, INV>(csub(a, b), k, 2 * h);
+            }
+        }
+    }
+    // undo the bit reversal of the radix-2 cascade
+    C t[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        int r = 0;
+#pragma unroll
+        for (int b = 1, x = i; b < R; b <<= 1, x >>= 1) r = (r << 1) | (x & 1);
+        t[i] = v[r];
+    }
+#pragma unroll
+    for (int i = 0; i < R; ++i) v[i] = t[i];
+}
+
+// One stage over all batches.  Element (j, b, mm) lives at
+// data[j * js + b * bs + mm * ms]; b < 2^logb; mm < MI is looped per thread.
+// BFAST: consecutive threads take consecutive b (else consecutive j).
+template <typename C, int R, int MI, bool INV, bool BFAST>
+__device__ __forceinline__ void fft_stage(C* data, int logn, int logns, int logb, int js, int bs, int ms,
+                                          const C* __restrict__ tw) {
+    constexpr int logR = R == 8 ? 3 : (R == 4 ? 2 : 1);
+    const int logm = logns - logR;
+    const int m = 1 << logm;
+    const int logitems_b = logn - logR;  // items per batch
+    const int total = 1 << (logitems_b + logb);
+    const int twshift = logn - logns;
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+        int b, i;
+        if (BFAST) {
+            b = t & ((1 << logb) - 1);
+            i = t >> logb;
+        } else {
+            i = t & ((1 << logitems_b) - 1);
+            b = t >> logitems_b;
+        }
+        const int j = i & (m - 1);
+        const int base = ((i >> logm) << logns) + j;
+        C w[R];
+#pragma unroll
+        for (int r = 1; r < R; ++r) w[r] = tw[(j * r) << twshift];
+        C* p = data + (long)base * js + (long)b * bs;
+#pragma unroll
+        for (int mm = 0; mm < MI; ++mm) {
+            C v[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[r] = p[(long)r * m * js + mm * ms];
+            if (!INV) {
+                small_dft<R, false>(v);
+#pragma unroll
+                for (int r = 1; r < R; ++r) v[r] = cmul(v[r], w[r]);
+            } else {
+#pragma unroll
+                for (int r = 1; r < R; ++r) v[r] = cmulc(v[r], w[r]);
+                small_dft<R, true>(v);
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r) p[(long)r * m * js + mm * ms] = v[r];
+        }
+    }
+    __syncthreads();
+}
+
+// Forward transform of length 2^logn (tw: 2^logn entries w_n^k).  Ends with
+// __syncthreads(); callers must synchronise before it.
+template <typename C, int MI, bool BFAST>
+__device__ void fft_fwd(C* data, int logn, int logb, int js, int bs, int ms, const C* __restrict__ tw) {
+    const int ns = fft_nstages(logn);
+    int logns = logn;
+    for (int s = 0; s < ns; ++s) {
+        const int bits = fft_stage_bits(logn, s);
+        if (bits == 3) fft_stage<C, 8, MI, false, BFAST>(data, logn, logns, logb, js, bs, ms, tw);
+        else if (bits == 2) fft_stage<C, 4, MI, false, BFAST>(data, logn, logns, logb, js, bs, ms, tw);
+        else fft_stage<C, 2, MI, false, BFAST>(data, logn, logns, logb, js, bs, ms, tw);
+        logns -= bits;
+    }
+}
+
+// Inverse (unnormalised) transform: digit-reversed order in, natural out.
+template <typename C, int MI, bool BFAST>
+__device__ void fft_inv(C* data, int logn, int logb, int js, int bs, int ms, const C* __restrict__ tw) {
+    const int ns = fft_nstages(logn);
+    int logns = logn;
+    int lns[8];
+    for (int s = 0; s < ns; ++s) {
+        lns[s] = logns;
+        logns -= fft_stage_bits(logn, s);
+    }
+    for (int s = ns - 1; s >= 0; --s) {
+        const int bits = fft_stage_bits(logn, s);
+        if (bits == 3) fft_stage<C, 8, MI, true, BFAST>(data, logn, lns[s], logb, js, bs, ms, tw);
+        else if (bits == 2) fft_stage<C, 4, MI, true, BFAST>(data, logn, lns[s], logb, js, bs, ms, tw);
+        else fft_stage<C, 2, MI, true, BFAST>(data, logn, lns[s], logb, js, bs, ms, tw);
+    }
+}
+
+// ---- FP64 <-> FP32 on the integer pipe (the FP64 pipe of this GPU is narrow)
+
+// Round-to-nearest-even double -> float for the normal float range; values
+// below it become signed zero, values above it infinity (NaN too).
+__device__ __forceinline__ float d2f_int(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+    const unsigned sign = hi & 0x80000000u;
+    const int e = (int)((hi >> 20) & 0x7FFu) - 896;
+    const unsigned mant = ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+    const unsigned rest = lo & 0x1FFFFFFFu;
+    unsigned f = ((unsigned)e << 23) + mant;
+    f += (rest > 0x10000000u) | ((rest == 0x10000000u) & (mant & 1u));
+    f = e <= 0 ? 0u : f;
+    f = (e >= 255 || f >= 0x7F800000u) ? 0x7F800000u : f;
+    return __uint_as_float(sign | f);
+}
+
+// Exact float -> double for normal floats (subnormal floats become zero).
+__device__ __forceinline__ double f2d_int(float x) {
+    const unsigned b = __float_as_uint(x);
+    const unsigned sign = b & 0x80000000u;
+    const unsigned e = (b >> 23) & 0xFFu;
+    const unsigned mant = b & 0x7FFFFFu;
+    unsigned hi = sign | ((e + 896u) << 20) | (mant >> 3);
+    unsigned lo = mant << 29;
+    hi = e == 0 ? sign : hi;
+    lo = e == 0 ? 0u : lo;
+    hi = e == 255 ? (sign | 0x7FF00000u | (mant >> 3)) : hi;
+    return __hiloint2double((int)hi, (int)lo);
+}
+
+template <typename R> __device__ __forceinline__ R to_real(double x);
+template <> __device__ __forceinline__ float to_real<float>(double x) { return d2f_int(x); }
+template <> __device__ __forceinline__ double to_real<double>(double x) { return x; }
+__device__ __forceinline__ double to_double(float x) { return f2d_int(x); }
+__device__ __forceinline__ double to_double(double x) { return x; }
+
+}  // namespace ac

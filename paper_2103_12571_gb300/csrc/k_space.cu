@@ -2,10 +2,11 @@
 // time frequency l and node m (Algorithm 1, inner loop).  For the periodic
 // constant-coefficient A the solve is exact in the discrete Fourier basis:
 // x^2 = IFFT( FFT(x^1) / (1 - dT mu sigma(k)) ), sigma the stencil symbol.
-// The forward FFT is decimation-in-frequency (bit-reversed output) and the
-// inverse decimation-in-time (bit-reversed input), so no reordering pass is
-// needed: the division only needs the true wavenumber of each slot.
+// Forward FFTs leave the spectrum in digit-reversed order and the inverse
+// FFTs take it back from there, so no reordering pass is needed: the
+// division only needs the true wavenumber of each slot (digitrev).
 #include "common.cuh"
+#include "fft.cuh"
 #include "kernels.h"
 
 namespace ac {
@@ -30,12 +31,12 @@ __global__ void __launch_bounds__(512) k_space_1d(SpaceArgs a) {
     for (int i = threadIdx.x; i < n; i += blockDim.x) d[i] = x[i];
     __syncthreads();
     const C* tw = reinterpret_cast<const C*>(a.tw_x);
-    fft_dif<C, false>(d, logn, 1, 0, 1, 0, tw);
+    fft_fwd<C, 1, false>(d, logn, 0, 1, 0, 0, tw);
     const C mu = reinterpret_cast<const C*>(a.mu_dT)[blockIdx.x];
     const C* sig = reinterpret_cast<const C*>(a.sig_x);
-    for (int i = threadIdx.x; i < n; i += blockDim.x) d[i] = shift_div(d[i], mu, sig[bitrev(i, logn)]);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) d[digitrev(i, logn)] = shift_div(d[digitrev(i, logn)], mu, sig[i]);
     __syncthreads();
-    fft_dit_inv<C, false>(d, logn, 1, 0, 1, 0, tw);
+    fft_inv<C, 1, false>(d, logn, 0, 1, 0, 0, tw);
     const R sc = (R)1 / (R)n;
     for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] = cscale(d[i], sc);
 }
@@ -54,51 +55,50 @@ __global__ void __launch_bounds__(512) k_space_2d_small(SpaceArgs a) {
     __syncthreads();
     const C* twx = reinterpret_cast<const C*>(a.tw_x);
     const C* twy = reinterpret_cast<const C*>(a.tw_y);
-    fft_dif<C, false>(d, lx, ny, -1, 1, nx, twx);            // rows
-    fft_dif<C, true>(d, ly, nx, lx, nx, 1, twy);             // columns
+    fft_fwd<C, 1, false>(d, lx, ly, 1, nx, 0, twx);   // rows (x index fastest across threads)
+    fft_fwd<C, 1, true>(d, ly, lx, nx, 1, 0, twy);    // columns (column index fastest)
     const C mu = reinterpret_cast<const C*>(a.mu_dT)[blockIdx.x];
     const C* sx = reinterpret_cast<const C*>(a.sig_x);
     const C* sy = reinterpret_cast<const C*>(a.sig_y);
     for (long i = threadIdx.x; i < N; i += blockDim.x) {
-        const int iy = (int)(i >> lx), ix = (int)(i & (nx - 1));
-        const C s = cadd(sx[bitrev(ix, lx)], sy[bitrev(iy, ly)]);
-        d[i] = shift_div(d[i], mu, s);
+        const int ky = (int)(i >> lx), kx = (int)(i & (nx - 1));
+        const long slot = ((long)digitrev(ky, ly) << lx) + digitrev(kx, lx);
+        d[slot] = shift_div(d[slot], mu, cadd(sx[kx], sy[ky]));
     }
     __syncthreads();
-    fft_dit_inv<C, true>(d, ly, nx, lx, nx, 1, twy);
-    fft_dit_inv<C, false>(d, lx, ny, -1, 1, nx, twx);
+    fft_inv<C, 1, true>(d, ly, lx, nx, 1, 0, twy);
+    fft_inv<C, 1, false>(d, lx, ly, 1, nx, 0, twx);
     const R sc = (R)1 / (R)N;
     for (long i = threadIdx.x; i < N; i += blockDim.x) x[i] = cscale(d[i], sc);
 }
 
 // Row pass of the three-pass 2D path: rows_per_block contiguous rows of length
-// nx; forward DIF, or inverse DIT with the 1/(nx ny) normalisation.
+// nx; forward FFT, or inverse FFT with the 1/(nx ny) normalisation.
 template <typename R>
 __global__ void __launch_bounds__(256) k_space_rows(SpaceArgs a, int inverse) {
     typedef typename Cx<R>::T C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* d = reinterpret_cast<C*>(smem_raw);
     const int nx = a.nx, rpb = a.rows_per_block;
-    const long total_rows = (long)a.planes * a.ny;
-    const long r0 = (long)blockIdx.x * rpb;
-    const int nr = (int)((total_rows - r0) < rpb ? (total_rows - r0) : rpb);
+    const int logr = 31 - __clz(rpb);
+    const long r0 = (long)blockIdx.x * rpb;   // rows_per_block divides planes * ny
     C* x = reinterpret_cast<C*>(a.X) + r0 * nx;
-    const long cnt = (long)nr * nx;
+    const long cnt = (long)rpb * nx;
     for (long i = threadIdx.x; i < cnt; i += blockDim.x) d[i] = x[i];
     __syncthreads();
     const C* tw = reinterpret_cast<const C*>(a.tw_x);
     if (!inverse) {
-        fft_dif<C, false>(d, a.lognx, nr, -1, 1, nx, tw);
+        fft_fwd<C, 1, false>(d, a.lognx, logr, 1, nx, 0, tw);
         for (long i = threadIdx.x; i < cnt; i += blockDim.x) x[i] = d[i];
     } else {
-        fft_dit_inv<C, false>(d, a.lognx, nr, -1, 1, nx, tw);
+        fft_inv<C, 1, false>(d, a.lognx, logr, 1, nx, 0, tw);
         const R sc = (R)1 / ((R)nx * (R)a.ny);
         for (long i = threadIdx.x; i < cnt; i += blockDim.x) x[i] = cscale(d[i], sc);
     }
 }
 
-// Column pass: a tile of W consecutive (bit-reversed) x slots times all ny
-// rows of one plane; forward DIF along y, divide, inverse DIT along y.
+// Column pass: a tile of W consecutive x slots (digit-reversed order) times
+// all ny rows of one plane; forward FFT along y, divide, inverse FFT along y.
 template <typename R>
 __global__ void __launch_bounds__(256) k_space_cols(SpaceArgs a) {
     typedef typename Cx<R>::T C;
@@ -117,17 +117,18 @@ __global__ void __launch_bounds__(256) k_space_cols(SpaceArgs a) {
     }
     __syncthreads();
     const C* twy = reinterpret_cast<const C*>(a.tw_y);
-    fft_dif<C, true>(d, a.logny, W, logW, W, 1, twy);
+    fft_fwd<C, 1, true>(d, a.logny, logW, W, 1, 0, twy);
     const C mu = reinterpret_cast<const C*>(a.mu_dT)[plane];
     const C* sx = reinterpret_cast<const C*>(a.sig_x);
     const C* sy = reinterpret_cast<const C*>(a.sig_y);
+    // wavenumber of each x slot in this tile and of each y slot
     for (long i = threadIdx.x; i < cnt; i += blockDim.x) {
-        const int iy = (int)(i >> logW), w = (int)(i & (W - 1));
-        const C s = cadd(sx[bitrev(c0 + w, a.lognx)], sy[bitrev(iy, a.logny)]);
-        d[i] = shift_div(d[i], mu, s);
+        const int ky = (int)(i >> logW), w = (int)(i & (W - 1));
+        const long slot = ((long)digitrev(ky, a.logny) << logW) + w;
+        d[slot] = shift_div(d[slot], mu, cadd(sx[slot_freq(c0 + w, a.lognx)], sy[ky]));
     }
     __syncthreads();
-    fft_dit_inv<C, true>(d, a.logny, W, logW, W, 1, twy);
+    fft_inv<C, 1, true>(d, a.logny, logW, W, 1, 0, twy);
     for (long i = threadIdx.x; i < cnt; i += blockDim.x) {
         const int iy = (int)(i >> logW), w = (int)(i & (W - 1));
         x[(long)iy * nx + w] = d[i];
@@ -166,7 +167,7 @@ cudaError_t launch_space_rows(const SpaceArgs& a, int inverse, cudaStream_t st) 
     cudaError_t e = set_smem(k_space_rows<R>, smem);
     if (e != cudaSuccess) return e;
     long rows = (long)a.planes * a.ny;
-    int grid = (int)((rows + a.rows_per_block - 1) / a.rows_per_block);
+    int grid = (int)(rows / a.rows_per_block);
     k_space_rows<R><<<grid, 256, smem, st>>>(a, inverse);
     return cudaGetLastError();
 }

@@ -5,15 +5,17 @@
 //   (Algorithm 1, lines computing r~ and x), and the node mixing
 //   x^1 = S_l^{-1} x of eq. (d1).  One CTA owns P grid points and all L*M
 //   values at each of them; the residual is written into shared memory in
-//   the transform precision, the FFT runs there (radix-2 DIF, bit-reversed
-//   output, which the per-frequency work does not care about), and only the
+//   the transform precision, the FFT runs there (mixed radix 8/4/2, DIF,
+//   digit-reversed output, which the per-frequency work does not care
+//   about), and only the
 //   F = L/2 + 1 non-redundant frequencies of the real data are stored.
 //   Two real columns are transformed as one complex column.
 // k_upd: eq. (d3) and (Gsubstitution) as one mix y = P_l x^2 with
-//   P_l = G_l^{-1} S_l, the inverse FFT along time of eq. (s3) (radix-2 DIT
-//   from bit-reversed order), the un-scaling by J, and the FP64 update
+//   P_l = G_l^{-1} S_l, the inverse FFT along time of eq. (s3) (DIT from
+//   digit-reversed order), the un-scaling by J, and the FP64 update
 //   u += e of the correction form of eq. (Riteration).
 #include "common.cuh"
+#include "fft.cuh"
 #include "kernels.h"
 
 namespace ac {
@@ -125,34 +127,34 @@ __global__ void __launch_bounds__(256) k_fwd(FwdArgs a) {
     float sq = 0.f;
     for (int l = threadIdx.x >> logP; l < L; l += blockDim.x >> logP) {
         double r[MM];
+        R rv[MM];
         if (n < N) {
             residual_point<MM>(a, l, n, dxo, dyo, r);
             const float isw = a.inv_s_w[l];
 #pragma unroll
             for (int m = 0; m < MM; ++m) {
-                const float rf = (float)r[m] * isw;
+                rv[m] = to_real<R>(r[m]);
+                const float rf = (sizeof(R) == 4 ? (float)rv[m] : d2f_int(r[m])) * isw;
                 sq = fmaf(rf, rf, sq);
             }
         } else {
 #pragma unroll
-            for (int m = 0; m < MM; ++m) r[m] = 0.0;
+            for (int m = 0; m < MM; ++m) rv[m] = (R)0;
         }
 #pragma unroll
-        for (int m = 0; m < MM; ++m) Zr[((long)l * MM + m) * P + p] = (R)r[m];
+        for (int m = 0; m < MM; ++m) Zr[((long)l * MM + m) * P + p] = rv[m];
     }
     __syncthreads();
 
-    const int nb = MM * HP;
-    const int lognb = (nb & (nb - 1)) == 0 ? 31 - __clz(nb) : -1;
-    fft_dif<C, true>(Z, a.logL, nb, lognb, nb, 1, reinterpret_cast<const C*>(a.tw));
+    const int logHP = logP - 1;
+    fft_fwd<C, MM, true>(Z, a.logL, logHP, MM * HP, 1, HP, reinterpret_cast<const C*>(a.tw));
 
     const C* Sinv = reinterpret_cast<const C*>(a.Sinv);
     C* X = reinterpret_cast<C*>(a.X);
-    const int logHP = logP - 1;
     const R half = (R)0.5;
     for (int idx = threadIdx.x; idx < a.F * HP; idx += blockDim.x) {
         const int k = idx >> logHP, q = idx & (HP - 1);
-        const int pk = bitrev(k, a.logL), pn = bitrev((L - k) & (L - 1), a.logL);
+        const int pk = digitrev(k, a.logL), pn = digitrev((L - k) & (L - 1), a.logL);
         const bool realbin = (k == 0) || (2 * k == L);
         C A[MM], B[MM];
 #pragma unroll
@@ -208,7 +210,7 @@ __global__ void __launch_bounds__(256) k_upd(UpdArgs a) {
         }
         const C* Pk = Pm + (long)k * MM * MM;
         const bool realbin = (k == 0) || (2 * k == L);
-        const int pk = bitrev(k, a.logL), pn = bitrev((L - k) & (L - 1), a.logL);
+        const int pk = digitrev(k, a.logL), pn = digitrev((L - k) & (L - 1), a.logL);
 #pragma unroll
         for (int m = 0; m < MM; ++m) {
             C ya = cmake((R)0, (R)0), yb = ya;
@@ -226,39 +228,32 @@ __global__ void __launch_bounds__(256) k_upd(UpdArgs a) {
     }
     __syncthreads();
 
-    const int nb = MM * HP;
-    const int lognb = (nb & (nb - 1)) == 0 ? 31 - __clz(nb) : -1;
-    fft_dit_inv<C, true>(Z, a.logL, nb, lognb, nb, 1, reinterpret_cast<const C*>(a.tw));
+    fft_inv<C, MM, true>(Z, a.logL, logHP, MM * HP, 1, HP, reinterpret_cast<const C*>(a.tw));
 
     float emax = 0.f;
-    for (int idx = threadIdx.x; idx < L * nb; idx += blockDim.x) {
-        const int l = idx / nb;
-        const int rem = idx - l * nb;
-        const int m = rem >> logHP, q = rem & (HP - 1);
+    const bool pairs = (N & 1) == 0;
+    for (int idx = threadIdx.x; idx < L * MM * HP; idx += blockDim.x) {
+        const int q = idx & (HP - 1);
+        const int lm = idx >> logHP;
+        const int l = lm / MM, m = lm - l * MM;
         const C z = Z[idx];
         const long nn = n0 + 2 * q;
         const double sv = a.sinv[l];
         double* o = a.out + ((long)l * MM + m) * N + nn;
-        const double ea = sv * (double)z.x, eb = sv * (double)z.y;
-        if (nn + 1 < N && (N & 1) == 0) {
-            if (a.accumulate) {
-                double2 v = *reinterpret_cast<double2*>(o);
-                v.x += ea;
-                v.y += eb;
-                *reinterpret_cast<double2*>(o) = v;
-            } else {
-                *reinterpret_cast<double2*>(o) = make_double2(ea, eb);
-            }
-            if (l == L - 1) emax = fmaxf(emax, fmaxf(fabsf((float)ea), fabsf((float)eb)));
+        const double za = to_double(z.x), zb = to_double(z.y);
+        if (l == L - 1) {
+            const float zx = sizeof(R) == 4 ? (float)z.x : d2f_int((double)z.x);
+            const float zy = sizeof(R) == 4 ? (float)z.y : d2f_int((double)z.y);
+            emax = fmaxf(emax, fmaxf(fabsf(zx), fabsf(zy)) * d2f_int(sv));
+        }
+        if (nn + 1 < N && pairs) {
+            double2 v = a.accumulate ? *reinterpret_cast<double2*>(o) : make_double2(0.0, 0.0);
+            v.x = fma(sv, za, v.x);
+            v.y = fma(sv, zb, v.y);
+            *reinterpret_cast<double2*>(o) = v;
         } else {
-            if (nn < N) {
-                o[0] = a.accumulate ? o[0] + ea : ea;
-                if (l == L - 1) emax = fmaxf(emax, fabsf((float)ea));
-            }
-            if (nn + 1 < N) {
-                o[1] = a.accumulate ? o[1] + eb : eb;
-                if (l == L - 1) emax = fmaxf(emax, fabsf((float)eb));
-            }
+            if (nn < N) o[0] = fma(sv, za, a.accumulate ? o[0] : 0.0);
+            if (nn + 1 < N) o[1] = fma(sv, zb, a.accumulate ? o[1] : 0.0);
         }
     }
     const float tot = block_max(emax, red);
