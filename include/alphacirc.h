@@ -182,6 +182,30 @@ int ac_adjoint_solve(ac_plan* plan, const double* g, double* lam, double tol,
 int ac_grad_params(ac_plan* plan, const double* u, const double* lam,
                    double* du0, double* dparams, void* stream);
 
+/* ---- preconditioner solve without device allocation --------------------- */
+
+/* No counterpart in the paper.  e = C_alpha^{-1} r exactly as ac_precond_solve
+ * computes it (same kernels, same precision choices), for callers that cannot
+ * allocate device memory when they need a solve -- e.g. code whose device
+ * memory is entirely owned by another framework's caching allocator, or a
+ * latency-critical loop that must not pay for the implicit synchronisation of
+ * cudaMalloc/cudaFree.  No plan is needed and nothing is allocated: every
+ * buffer and table the solve uses is carved out of one fixed 32 MiB device
+ * array inside this library, which each GPU that loads the library keeps
+ * until the process exits.
+ *   prob, M, L, dT: as for ac_setup (FFT inner solve, power-of-two grid, L a
+ *     power of two in 2..1024, M in 1..4); precision: AC_C128 or AC_C64.
+ *   alpha in (0,1).  r, e: device, L*M*N doubles (may be the same buffer).
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  All calls on a device share the array: calls whose GPU work may
+ * overlap (other streams, other host threads) race and must be ordered by the
+ * caller.  Problems whose buffers do not fit in 32 MiB are rejected with
+ * AC_ERR_INVALID_ARG and a message naming the size needed (ac_last_error). */
+int ac_precond_solve_noalloc(const ac_problem* prob, int M, int L, double dT,
+                             double alpha, int precision, const double* r,
+                             double* e, void* stream);
+
 /* ---- host-side planner (no GPU needed) ---------------------------------- */
 
 /* Radau IIA nodes 0 < t_1 < ... < t_M = 1 (roots of P_{M-1} + P_M mapped by

@@ -36,6 +36,9 @@ static int fail(int code, const char* fmt, ...) {
     return code;
 }
 
+// lets the allocation-free entry point (noalloc.cu) report through ac_last_error
+void ac_internal_set_error(const char* msg) { g_err = msg; }
+
 #define CK(call)                                                                              \
     do {                                                                                      \
         cudaError_t e_ = (call);                                                              \

@@ -1,0 +1,295 @@
+// A preconditioner solve that allocates no device memory.
+//
+// Some callers cannot allocate device memory at the moment they need a solve:
+// for example code whose whole device memory has been handed to another
+// framework's caching allocator (so cudaMalloc would fail or fragment that
+// pool), or a latency-critical loop in which the implicit device
+// synchronisation of cudaMalloc/cudaFree is not acceptable.  Such callers
+// cannot build an ac_plan, because ac_setup allocates its workspace.
+// ac_precond_solve_noalloc gives them e = C_alpha^{-1} r with every piece of
+// working memory -- the complex F*M*N transform buffer, the twiddle, symbol
+// and eigenbasis tables and the block partial sums -- carved out of one
+// file-scope device array of fixed size.  It runs the same kernels as
+// ac_precond_solve.
+//
+// The array lives in every GPU that loads the library until the process
+// exits.  All calls on a device share it: two calls whose GPU work overlaps
+// (different streams, or different host threads) race on it, so callers must
+// order them.  Nothing in it has to start at zero: every call rewrites all of
+// the regions it reads.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "alphacirc.h"
+#include "kernels.h"
+#include "planner.h"
+
+namespace {
+
+constexpr size_t kScratchBytes = size_t(32) << 20;  // 32 MiB per device
+static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
+
+constexpr int kMaxDevices = 64;
+struct DeviceScratch {
+    std::once_flag once;
+    void* ptr = nullptr;
+    cudaError_t err = cudaSuccess;
+};
+DeviceScratch g_dev[kMaxDevices];
+
+}  // namespace
+
+// message for ac_last_error(), kept by the C ABI layer
+void ac_internal_set_error(const char* msg);
+
+namespace {
+
+int nfail(int code, const char* msg) {
+    std::string m = std::string("ac_precond_solve_noalloc: ") + msg;
+    ac_internal_set_error(m.c_str());
+    return code;
+}
+
+// Device address of the scratch array on the current device.  Host code must
+// not pass g_scratch itself to a kernel: on the host that name is only a
+// stand-in.  The address is looked up once per device, with that device
+// current.
+int scratch_address(unsigned char** out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nfail(AC_ERR_CUDA, "cudaGetDevice failed");
+    if (dev < 0 || dev >= kMaxDevices) return nfail(AC_ERR_INVALID_ARG, "device ordinal out of range");
+    DeviceScratch& d = g_dev[dev];
+    std::call_once(d.once, [&d]() { d.err = cudaGetSymbolAddress(&d.ptr, g_scratch); });
+    if (d.err != cudaSuccess || !d.ptr) return nfail(AC_ERR_CUDA, "cudaGetSymbolAddress of the scratch array failed");
+    *out = static_cast<unsigned char*>(d.ptr);
+    return AC_OK;
+}
+
+size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+bool pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+int log2i(int v) {
+    int l = 0;
+    while ((1 << l) < v) ++l;
+    return l;
+}
+
+// host complex table -> device, in the transform precision
+cudaError_t put_c(void* dst, const std::vector<ac::cd>& v, bool dbl, cudaStream_t st) {
+    if (dbl) return cudaMemcpyAsync(dst, v.data(), v.size() * sizeof(ac::cd), cudaMemcpyHostToDevice, st);
+    std::vector<float> f(2 * v.size());
+    for (size_t i = 0; i < v.size(); ++i) {
+        f[2 * i] = (float)v[i].real();
+        f[2 * i + 1] = (float)v[i].imag();
+    }
+    return cudaMemcpyAsync(dst, f.data(), f.size() * sizeof(float), cudaMemcpyHostToDevice, st);
+}
+
+template <typename R>
+int run(const ac_problem* prob, int M, int L, double dT, double alpha, const double* r, double* e,
+        cudaStream_t st) {
+    const bool dbl = sizeof(R) == 8;
+    const size_t cs = 2 * sizeof(R);
+    const int nx = prob->nx, ny = prob->dim == 2 ? prob->ny : 1;
+    const long long N = (long long)nx * ny;
+    const int F = L / 2 + 1;
+
+    // spatial path and time tile, chosen as ac_setup chooses them
+    int path, rpb = 1, W = 1;
+    if (prob->dim == 1) {
+        if ((size_t)nx * cs > 160 * 1024) return nfail(AC_ERR_INVALID_ARG, "1D grid too large");
+        path = 0;
+    } else if ((size_t)nx * ny * cs <= 160 * 1024) {
+        path = 1;
+    } else {
+        path = 2;
+        rpb = (int)(32768 / ((size_t)nx * cs));
+        if (rpb < 1) rpb = 1;
+        while (rpb & (rpb - 1)) rpb &= rpb - 1;
+        if (rpb > ny) rpb = ny;
+        W = (int)(128 / cs);
+        if (W > nx) W = nx;
+        if ((size_t)nx * cs > 160 * 1024 || (size_t)ny * W * cs > 160 * 1024)
+            return nfail(AC_ERR_INVALID_ARG, "2D grid too large");
+    }
+    int P = 256;
+    while (P > 2 && (size_t)L * M * P * sizeof(R) > 50 * 1024) P >>= 1;
+    while (P > 16 && (N + P - 1) / P < 2 * 152) P >>= 1;
+    if ((size_t)L * M * P * sizeof(R) > 200 * 1024) return nfail(AC_ERR_INVALID_ARG, "L*M too large");
+    const int grid = (int)((N + P - 1) / P);
+
+    // carve the scratch array
+    size_t off = 0;
+    auto take = [&off](size_t bytes) {
+        size_t o = off;
+        off = align256(off + bytes);
+        return o;
+    };
+    const size_t oX = take((size_t)F * M * N * cs);
+    const size_t otwL = take((size_t)L * cs), otwx = take((size_t)nx * cs), otwy = take((size_t)ny * cs);
+    const size_t osx = take((size_t)nx * cs), osy = take((size_t)ny * cs);
+    const size_t oqs = take(sizeof(double) * (size_t)L * M * M), os = take(sizeof(double) * L);
+    const size_t oisw = take(sizeof(float) * L), osinv = take(sizeof(double) * L);
+    const size_t oSinv = take((size_t)F * M * M * cs), oP = take((size_t)F * M * M * cs);
+    const size_t omu = take((size_t)F * M * cs);
+    const size_t opf = take(sizeof(float) * grid), opu = take(sizeof(float) * grid);
+    if (off > kScratchBytes) {
+        char msg[256];
+        std::snprintf(msg, sizeof(msg),
+                      "problem needs %.1f MiB of scratch; the fixed no-allocation scratch holds %zu MiB "
+                      "(use ac_setup + ac_precond_solve instead)",
+                      off / 1048576.0, kScratchBytes >> 20);
+        return nfail(AC_ERR_INVALID_ARG, msg);
+    }
+    unsigned char* base = nullptr;
+    int rc = scratch_address(&base);
+    if (rc) return rc;
+
+    // host tables (Radau IIA data, stencil, twiddles, alpha-dependent tables)
+    double t[8], Q[64];
+    ac::radau_nodes(M, t);
+    ac::collocation_matrix(M, t, Q);
+    double tx[5] = {0}, ty[5] = {0};
+    ac::axis_taps(prob->order, nx, prob->lx, prob->nu, prob->cx, tx);
+    if (prob->dim == 2) ac::axis_taps(prob->order, ny, prob->ly, prob->nu, prob->cy, ty);
+    auto tw = [](int n) {
+        std::vector<ac::cd> v(n);
+        for (int k = 0; k < n; ++k) v[k] = std::exp(ac::cd(0.0, -2.0 * M_PI * k / n));
+        return v;
+    };
+    std::vector<ac::cd> sx(nx), sy(ny, ac::cd(0.0));
+    ac::axis_symbol(nx, tx, sx.data());
+    if (prob->dim == 2) ac::axis_symbol(ny, ty, sy.data());
+    std::vector<double> qs((size_t)L * M * M), s(L), sinv(L);
+    std::vector<float> isw(L);
+    for (int l = 0; l < L; ++l) {
+        s[l] = l == 0 ? 1.0 : std::pow(alpha, (double)l / L);
+        sinv[l] = (l == 0 ? 1.0 : std::pow(alpha, -(double)l / L)) / L;
+        isw[l] = (float)(1.0 / s[l]);
+        for (int m = 0; m < M; ++m)
+            for (int j = 0; j < M; ++j) qs[((size_t)l * M + m) * M + j] = s[l] * dT * Q[m * M + j];
+    }
+    std::vector<ac::cd> mu((size_t)F * M), Sinv((size_t)F * M * M), Pm((size_t)F * M * M);
+    double worst = ac::freq_tables(M, L, alpha, false, Q, t, mu.data(), Sinv.data(), Pm.data(), nullptr);
+    if (worst < 0 || worst > 1e10) return nfail(AC_ERR_NOT_DIAGONALIZABLE, "Q G_l^{-1} not diagonalisable");
+    for (auto& v : mu) v *= dT;
+
+    cudaError_t ce = cudaSuccess;
+    auto chk = [&ce](cudaError_t x) {
+        if (ce == cudaSuccess) ce = x;
+    };
+    chk(put_c(base + otwL, tw(L), dbl, st));
+    chk(put_c(base + otwx, tw(nx), dbl, st));
+    chk(put_c(base + otwy, tw(ny), dbl, st));
+    chk(put_c(base + osx, sx, dbl, st));
+    chk(put_c(base + osy, sy, dbl, st));
+    chk(cudaMemcpyAsync(base + oqs, qs.data(), qs.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    chk(cudaMemcpyAsync(base + os, s.data(), s.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    chk(cudaMemcpyAsync(base + oisw, isw.data(), isw.size() * sizeof(float), cudaMemcpyHostToDevice, st));
+    chk(cudaMemcpyAsync(base + osinv, sinv.data(), sinv.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    chk(put_c(base + oSinv, Sinv, dbl, st));
+    chk(put_c(base + oP, Pm, dbl, st));
+    chk(put_c(base + omu, mu, dbl, st));
+    if (ce != cudaSuccess) return nfail(AC_ERR_CUDA, cudaGetErrorString(ce));
+
+    ac::Grid g;
+    g.dim = prob->dim;
+    g.nx = nx;
+    g.ny = ny;
+    g.N = (int)N;
+    g.rad = prob->order == 4 ? 2 : 1;
+    for (int i = 0; i < 5; ++i) {
+        g.tx[i] = tx[i];
+        g.ty[i] = ty[i];
+    }
+    g.c0 = tx[2] + ty[2];
+
+    ac::FwdArgs fa;
+    fa.g = g;
+    fa.M = M;
+    fa.L = L;
+    fa.logL = log2i(L);
+    fa.F = F;
+    fa.P = P;
+    fa.u = nullptr;
+    fa.u0 = nullptr;
+    fa.b = r;
+    fa.b_reversed = 0;
+    fa.transposed = 0;
+    fa.qs = reinterpret_cast<const double*>(base + oqs);
+    fa.s = reinterpret_cast<const double*>(base + os);
+    fa.inv_s_w = reinterpret_cast<const float*>(base + oisw);
+    fa.tw = base + otwL;
+    fa.Sinv = base + oSinv;
+    fa.X = base + oX;
+    fa.part = reinterpret_cast<float*>(base + opf);
+    const size_t smem = (size_t)L * M * P * sizeof(R);
+    chk(ac::launch_fwd<R>(fa, grid, smem, st));
+
+    ac::SpaceArgs sa;
+    sa.nx = nx;
+    sa.ny = ny;
+    sa.lognx = log2i(nx);
+    sa.logny = log2i(ny);
+    sa.planes = F * M;
+    sa.M = M;
+    sa.X = base + oX;
+    sa.mu_dT = base + omu;
+    sa.sig_x = base + osx;
+    sa.sig_y = base + osy;
+    sa.tw_x = base + otwx;
+    sa.tw_y = base + otwy;
+    sa.rows_per_block = rpb;
+    sa.cols_per_block = W;
+    if (path == 0) chk(ac::launch_space_1d<R>(sa, st));
+    else if (path == 1) chk(ac::launch_space_2d_small<R>(sa, st));
+    else {
+        chk(ac::launch_space_rows<R>(sa, 0, st));
+        chk(ac::launch_space_cols<R>(sa, st));
+        chk(ac::launch_space_rows<R>(sa, 1, st));
+    }
+
+    ac::UpdArgs ua;
+    ua.N = (int)N;
+    ua.M = M;
+    ua.L = L;
+    ua.logL = log2i(L);
+    ua.F = F;
+    ua.P = P;
+    ua.X = base + oX;
+    ua.Pm = base + oP;
+    ua.tw = base + otwL;
+    ua.sinv = reinterpret_cast<const double*>(base + osinv);
+    ua.out = e;
+    ua.accumulate = 0;
+    ua.part = reinterpret_cast<float*>(base + opu);
+    chk(ac::launch_upd<R>(ua, grid, smem, st));
+    if (ce != cudaSuccess) return nfail(AC_ERR_CUDA, cudaGetErrorString(ce));
+    return AC_OK;
+}
+
+}  // namespace
+
+extern "C" int ac_precond_solve_noalloc(const ac_problem* prob, int M, int L, double dT, double alpha,
+                                        int precision, const double* r, double* e, void* stream) {
+    if (!prob || !r || !e) return nfail(AC_ERR_INVALID_ARG, "null argument");
+    if (prob->dim != 1 && prob->dim != 2) return nfail(AC_ERR_INVALID_ARG, "dim must be 1 or 2");
+    if (prob->order != 2 && prob->order != 4) return nfail(AC_ERR_INVALID_ARG, "order must be 2 or 4");
+    const int ny = prob->dim == 2 ? prob->ny : 1;
+    if (prob->nx < 2 || (prob->dim == 2 && ny < 2) || !pow2(prob->nx) || !pow2(ny))
+        return nfail(AC_ERR_INVALID_ARG, "grid sizes must be powers of two >= 2");
+    if (M < 1 || M > 4) return nfail(AC_ERR_INVALID_ARG, "M must be 1..4");
+    if (!pow2(L) || L < 2 || L > 1024) return nfail(AC_ERR_INVALID_ARG, "L must be a power of two in 2..1024");
+    if (!(dT > 0)) return nfail(AC_ERR_INVALID_ARG, "dT must be positive");
+    if (!(alpha > 0.0) || !(alpha < 1.0)) return nfail(AC_ERR_INVALID_ARG, "alpha must be in (0,1)");
+    if (!(prob->lx > 0) || (prob->dim == 2 && !(prob->ly > 0))) return nfail(AC_ERR_INVALID_ARG, "bad box length");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (precision == AC_C128) return run<double>(prob, M, L, dT, alpha, r, e, st);
+    if (precision == AC_C64) return run<float>(prob, M, L, dT, alpha, r, e, st);
+    return nfail(AC_ERR_INVALID_ARG, "bad precision");
+}
