@@ -79,6 +79,7 @@ typedef struct {
     double tau;       /* inner-solve relative tolerance (BiCGStab), used in gamma too */
     int max_iter;     /* outer iteration cap (<= AC_MAX_STATS)                        */
     int stop_rule;    /* AC_STOP_RESIDUAL | AC_STOP_PAPER                             */
+    int inner_max_iter; /* BiCGStab iteration cap per system (<= 0: 4000)             */
 } ac_alpha_schedule;
 
 /* Per-solve record (host memory, filled by the solve calls). */
@@ -90,6 +91,7 @@ typedef struct {
     double m[AC_MAX_STATS];           /* Algorithm 2's m_k (0 for other modes)          */
     double diff_last[AC_MAX_STATS];   /* ||u_L^{(k+1)} - u_L^{(k)}||_inf                 */
     int inner_iters[AC_MAX_STATS];    /* BiCGStab: max iterations over systems, per k   */
+    int inner_failed[AC_MAX_STATS];   /* BiCGStab: systems that stopped above tau, per k */
     double w_norm2;                   /* ||w||_2                                         */
     double w_inf;                     /* ||w||_inf                                       */
 } ac_stats;

@@ -33,14 +33,16 @@ class Problem(ctypes.Structure):
 
 class Schedule(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int), ("alpha0", ctypes.c_double), ("m0", ctypes.c_double),
-                ("tau", ctypes.c_double), ("max_iter", ctypes.c_int), ("stop_rule", ctypes.c_int)]
+                ("tau", ctypes.c_double), ("max_iter", ctypes.c_int), ("stop_rule", ctypes.c_int),
+                ("inner_max_iter", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("converged", ctypes.c_int),
                 ("res_rel", ctypes.c_double * AC_MAX_STATS), ("alpha", ctypes.c_double * AC_MAX_STATS),
                 ("m", ctypes.c_double * AC_MAX_STATS), ("diff_last", ctypes.c_double * AC_MAX_STATS),
-                ("inner_iters", ctypes.c_int * AC_MAX_STATS), ("w_norm2", ctypes.c_double),
+                ("inner_iters", ctypes.c_int * AC_MAX_STATS), ("inner_failed", ctypes.c_int * AC_MAX_STATS),
+                ("w_norm2", ctypes.c_double),
                 ("w_inf", ctypes.c_double)]
 
 

@@ -43,14 +43,15 @@ def stats_dict(st):
     k = st.iters
     return dict(iters=k, converged=bool(st.converged), res_rel=list(st.res_rel[:k + 1]),
                 alpha=list(st.alpha[:k]), m=list(st.m[:k + 1]), diff_last=list(st.diff_last[:k]),
-                inner_iters=list(st.inner_iters[:k]), w_norm2=st.w_norm2, w_inf=st.w_inf)
+                inner_iters=list(st.inner_iters[:k]), inner_failed=list(st.inner_failed[:k]),
+                w_norm2=st.w_norm2, w_inf=st.w_inf)
 
 
 class Plan:
     """Plan for a problem dict (see ``workloads.problem``) with M nodes, L steps."""
 
     def __init__(self, prob, M=None, L=None, dT=None, precision="c128", inner="fft", alpha="paper",
-                 alpha0=1e-4, m0=0.0, tau=0.0, max_iter=50, stop="residual"):
+                 alpha0=1e-4, m0=0.0, tau=0.0, max_iter=50, stop="residual", inner_max_iter=0):
         M = int(M if M is not None else prob["M"])
         L = int(L if L is not None else prob["L"])
         dT = float(dT if dT is not None else prob["T"] / L)
@@ -58,7 +59,7 @@ class Plan:
         self.N = int(prob["nx"]) * (int(prob.get("ny", 1)) if int(prob["dim"]) == 2 else 1)
         self.prob = dict(prob)
         sched = C.Schedule(mode=ALPHA[alpha], alpha0=float(alpha0), m0=float(m0), tau=float(tau),
-                           max_iter=int(max_iter), stop_rule=STOP[stop])
+                           max_iter=int(max_iter), stop_rule=STOP[stop], inner_max_iter=int(inner_max_iter))
         handle = ctypes.c_void_p()
         C.check(C.lib().ac_setup(ctypes.byref(make_problem(prob)), M, L, dT, ctypes.byref(sched),
                                  PRECISION[precision], INNER[inner], ctypes.byref(handle)), "ac_setup")

@@ -20,6 +20,7 @@ namespace ac {
 cudaError_t launch_wnorms(const double* u0, const double* b, int L, int M, long long N, double* part,
                           int grid, cudaStream_t st);
 cudaError_t launch_fill_stack(const double* u0, double* u, int L, int M, long long N, cudaStream_t st);
+cudaError_t launch_a_inf(const Grid& g, const double* u0, double* part, int grid, cudaStream_t st);
 }
 
 using ac::cd;
@@ -90,6 +91,10 @@ struct ac_plan {
     double* d_part_d = nullptr;  // FP64 reductions
     double* d_dtQ = nullptr;     // dT Q
     double* d_dtQT = nullptr;    // dT Q^T
+    void* d_bicg = nullptr;      // BiCGStab vectors when they do not fit in shared memory
+    int* d_iters = nullptr;      // BiCGStab iterations per system
+    int* h_iters = nullptr;      // pinned copy
+    bool iters_pending = false;
     float* h_part_fwd = nullptr;  // pinned
     float* h_part_upd = nullptr;
     double* h_part_d = nullptr;
@@ -224,6 +229,15 @@ static int ensure_tables(ac_plan* p, double alpha, int transposed, double wscale
     return AC_OK;
 }
 
+// Relative tolerance of the BiCGStab inner solves: the schedule's tau (1e-8
+// if unset), floored at 2^-20 in the complex64 form, where FP32 arithmetic
+// cannot certify a smaller relative residual.
+static double inner_tau(const ac_plan* p) {
+    double tau = p->sched.tau > 0 ? p->sched.tau : 1e-8;
+    if (p->precision == AC_C64) tau = std::max(tau, std::ldexp(1.0, -20));
+    return tau;
+}
+
 // ------------------------------------------------------ one preconditioner
 // out (+)= C_alpha^{-1} (w - C u)   [u may be null: out (+)= C_alpha^{-1} w]
 template <typename R>
@@ -286,6 +300,20 @@ static int stage_a(ac_plan* p, const double* u, const double* u0, const double* 
             CK(ac::launch_space_cols<R>(sa, st));
             CK(ac::launch_space_rows<R>(sa, 1, st));
             p->launches += 3;
+        } else if (p->spatial_path == 3) {
+            ac::BicgArgs ba;
+            ba.g = transposed ? p->grid_adj : p->grid_fwd;
+            ba.planes = p->F * p->M;
+            ba.M = p->M;
+            ba.max_iter = p->sched.inner_max_iter > 0 ? p->sched.inner_max_iter : 4000;
+            ba.tau = inner_tau(p);
+            ba.X = p->X;
+            ba.mu_dT = p->d_mu;
+            ba.iters = p->d_iters;
+            CK(ac::launch_bicgstab<R>(ba, p->d_bicg, st));
+            p->launches++;
+            CK(cudaMemcpyAsync(p->h_iters, p->d_iters, sizeof(int) * ba.planes, cudaMemcpyDeviceToHost, st));
+            p->iters_pending = true;
         } else {
             return fail(AC_ERR_INVALID_ARG, "inner solver path %d not available", p->spatial_path);
         }
@@ -356,6 +384,22 @@ static int w_norms(ac_plan* p, const double* u0, const double* b, double* n2, do
     return AC_OK;
 }
 
+// ||A u0||_inf (A^T for the transposed system) by a stencil kernel
+static int a_u0_inf(ac_plan* p, const double* u0, int transposed, double* out, cudaStream_t st) {
+    const int grid = 152 * 2;
+    {
+        ProfScope ps(p, KK_AUX, st);
+        CK(ac::launch_a_inf(transposed ? p->grid_adj : p->grid_fwd, u0, p->d_part_d, grid, st));
+        p->launches++;
+    }
+    CK(cudaMemcpyAsync(p->h_part_d, p->d_part_d, sizeof(double) * grid, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    double mx = 0.0;
+    for (int i = 0; i < grid; ++i) mx = std::max(mx, p->h_part_d[i]);
+    *out = mx;
+    return AC_OK;
+}
+
 static double a_inf_norm(const ac_plan* p) {
     double s = 0.0;
     for (int i = 0; i < 5; ++i) {
@@ -370,6 +414,25 @@ static double pow2_scale(double v) {
     int e;
     std::frexp(v, &e);
     return std::ldexp(1.0, e);
+}
+
+// Largest BiCGStab iteration count over the systems of the last inner solve,
+// and the number of systems that stopped above tau (cap, stagnation, breakdown).
+static int inner_summary(const ac_plan* p, int* failed) {
+    int worst = 0, bad = 0;
+    for (int i = 0; i < p->F * p->M; ++i) {
+        int v = p->h_iters[i];
+        if (v < 0) {
+            v = -v;
+            ++bad;
+        } else if (v >= 1000000) {
+            v %= 1000000;
+            ++bad;
+        }
+        worst = std::max(worst, v);
+    }
+    *failed = bad;
+    return worst;
 }
 
 // The Richardson loop shared by the forward and the adjoint solve.
@@ -393,9 +456,24 @@ static int richardson_loop(ac_plan* p, const double* u0, const double* b, int b_
     const ac_alpha_schedule& sc = p->sched;
     const int max_iter = std::min(std::max(sc.max_iter, 1), AC_MAX_STATS - 1);
     const double eps = p->precision == AC_C128 ? std::ldexp(1.0, -53) : std::ldexp(1.0, -24);
-    const double tau = p->inner == AC_INNER_BICGSTAB ? sc.tau : 0.0;
+    const double tau = p->inner == AC_INNER_BICGSTAB ? inner_tau(p) : 0.0;
     const double gam = p->L * (3.0 * eps + tau) * winf;
-    double m = sc.m0 > 0 ? sc.m0 : p->L * p->dT * a_inf_norm(p) * winf;
+    // m0 ~ ||u^(0) - u*||_inf: T max|u_t(0)| = T ||A u0 + b||_inf (Sec. 3.3, the
+    // Lipschitz estimate) when the caller gives none; for a zero initial
+    // iterate (adjoint) the bound L ||w||_inf
+    double m = sc.m0;
+    if (!(m > 0)) {
+        if (u0) {
+            double au0 = 0.0;
+            rc = a_u0_inf(p, u0, transposed, &au0, st);
+            if (rc) return rc;
+            m = p->L * p->dT * (au0 + (b ? winf : 0.0));
+        }
+        if (!(m > 0)) m = p->L * winf;
+    }
+    // in the correction form the per-iteration error factor is about
+    // alpha + L (3 eps + tau) / alpha, minimal at this alpha; Algorithm 2's
+    // alpha_k (which tend to 1/2) are capped there
     const double alpha_mixed = std::min(0.25, std::max(1e-8, std::sqrt(p->L * (3.0 * eps + tau))));
     int grew = 0;
     double prev_res = 1e300;
@@ -407,7 +485,7 @@ static int richardson_loop(ac_plan* p, const double* u0, const double* b, int b_
         else {
             alpha = std::sqrt(gam / m);          // alpha_{k+1} = sqrt(gamma / m_k)
             m_next = 2.0 * std::sqrt(m * gam);   // m_{k+1} = 2 sqrt(m_k gamma)
-            alpha = std::min(0.5, std::max(alpha, 1e-12));
+            alpha = std::min(alpha_mixed, std::max(alpha, 1e-12));
         }
         rc = ensure_tables(p, alpha, transposed, wscale, st);
         if (rc) return rc;
@@ -417,6 +495,7 @@ static int richardson_loop(ac_plan* p, const double* u0, const double* b, int b_
         rc = precond_a(p, u, u0, b, b_rev, transposed, st, true);
         if (rc) return rc;
         CK(cudaEventSynchronize(p->ev_res));
+        if (k > 0 && p->spatial_path == 3) S->inner_iters[k - 1] = inner_summary(p, &S->inner_failed[k - 1]);
         double s = 0.0;
         for (int i = 0; i < p->grid; ++i) s += p->h_part_fwd[i];
         const double res = std::sqrt(s) * wscale / wn2;
@@ -482,12 +561,14 @@ void ac_destroy(ac_plan* p) {
     for (auto e : p->pool) cudaEventDestroy(e);
     void* bufs[] = {p->X, p->tw_L, p->tw_x, p->tw_y, p->sig_x, p->sig_y, p->sigT_x, p->sigT_y,
                     p->d_qs, p->d_s, p->d_inv_s_w, p->d_sinv, p->d_Sinv, p->d_P, p->d_mu,
-                    p->d_part_fwd, p->d_part_upd, p->d_part_d, p->d_dtQ, p->d_dtQT};
+                    p->d_part_fwd, p->d_part_upd, p->d_part_d, p->d_dtQ, p->d_dtQT, p->d_bicg,
+                    p->d_iters};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (p->h_part_fwd) cudaFreeHost(p->h_part_fwd);
     if (p->h_part_upd) cudaFreeHost(p->h_part_upd);
     if (p->h_part_d) cudaFreeHost(p->h_part_d);
+    if (p->h_iters) cudaFreeHost(p->h_iters);
     if (p->ev_res) cudaEventDestroy(p->ev_res);
     delete p;
 }
@@ -589,8 +670,12 @@ int ac_setup(const ac_problem* prob, int M, int L, double dT, const ac_alpha_sch
             }
         }
     } else {
-        ac_destroy(p);
-        return fail(AC_ERR_INVALID_ARG, "BiCGStab inner solver not built into this library");
+        p->spatial_path = 3;
+        const int rad = prob->order == 4 ? 2 : 1;
+        if (prob->nx < 2 * rad + 1 || (prob->dim == 2 && ny < 2 * rad + 1)) {
+            ac_destroy(p);
+            return fail(AC_ERR_INVALID_ARG, "grid smaller than the stencil");
+        }
     }
 
     // tile of the time kernels: P points, L*M*P reals of shared memory
@@ -633,10 +718,15 @@ int ac_setup(const ac_problem* prob, int M, int L, double dT, const ac_alpha_sch
     AL(p->d_part_d, sizeof(double) * p->part_d_len);
     AL(p->d_dtQ, sizeof(double) * M * M);
     AL(p->d_dtQT, sizeof(double) * M * M);
+    if (p->spatial_path == 3) {
+        AL(p->d_iters, sizeof(int) * F * M);
+        if (6 * cs * (size_t)p->N > 200 * 1024) AL(p->d_bicg, 6 * cs * (size_t)p->N * F * M);
+    }
 #undef AL
     if (e == cudaSuccess) e = cudaMallocHost((void**)&p->h_part_fwd, sizeof(float) * p->grid);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&p->h_part_upd, sizeof(float) * p->grid);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&p->h_part_d, sizeof(double) * p->part_d_len);
+    if (e == cudaSuccess && p->spatial_path == 3) e = cudaMallocHost((void**)&p->h_iters, sizeof(int) * F * M);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_res, cudaEventBlockingSync);
     if (e != cudaSuccess) {
         int rc = fail(AC_ERR_CUDA, "allocation failed: %s", cudaGetErrorString(e));

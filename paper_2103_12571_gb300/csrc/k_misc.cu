@@ -248,6 +248,29 @@ cudaError_t launch_wnorms(const double* u0, const double* b, int L, int M, long 
     return cudaGetLastError();
 }
 
+// per-block max |A u0|
+__global__ void __launch_bounds__(256) k_a_inf(Grid g, const double* u0, double* part) {
+    __shared__ double red[32];
+    double mx = 0.0;
+    for (long n = blockIdx.x * (long)blockDim.x + threadIdx.x; n < g.N; n += (long)gridDim.x * blockDim.x) {
+        const Nbr b = neighbours(g, n);
+        mx = fmax(mx, fabs(stencil(u0 + n, b, g.rad, g.dim, g.tx, g.ty, g.c0)));
+    }
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double r = 0.0;
+        for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) r = fmax(r, red[w]);
+        part[blockIdx.x] = r;
+    }
+}
+
+cudaError_t launch_a_inf(const Grid& g, const double* u0, double* part, int grid, cudaStream_t st) {
+    k_a_inf<<<grid, 256, 0, st>>>(g, u0, part);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_fill_stack(const double* u0, double* u, int L, int M, long long N, cudaStream_t st) {
     const long total = (long)L * M * N;
     int grid = (int)((total + 255) / 256);

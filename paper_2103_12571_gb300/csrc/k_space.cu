@@ -81,19 +81,29 @@ __global__ void __launch_bounds__(256) k_space_rows(SpaceArgs a, int inverse) {
     C* d = reinterpret_cast<C*>(smem_raw);
     const int nx = a.nx, rpb = a.rows_per_block;
     const int logr = 31 - __clz(rpb);
+    const int ld = rpb + 1;                   // padded stride of the transposed layout d[x][row]
     const long r0 = (long)blockIdx.x * rpb;   // rows_per_block divides planes * ny
     C* x = reinterpret_cast<C*>(a.X) + r0 * nx;
     const long cnt = (long)rpb * nx;
-    for (long i = threadIdx.x; i < cnt; i += blockDim.x) d[i] = x[i];
+    for (long i = threadIdx.x; i < cnt; i += blockDim.x) {
+        const int row = (int)(i >> a.lognx), ix = (int)(i & (nx - 1));
+        d[ix * ld + row] = x[i];
+    }
     __syncthreads();
     const C* tw = reinterpret_cast<const C*>(a.tw_x);
     if (!inverse) {
-        fft_fwd<C, 1, false>(d, a.lognx, logr, 1, nx, 0, tw);
-        for (long i = threadIdx.x; i < cnt; i += blockDim.x) x[i] = d[i];
+        fft_fwd<C, 1, true>(d, a.lognx, logr, ld, 1, 0, tw);
+        for (long i = threadIdx.x; i < cnt; i += blockDim.x) {
+            const int row = (int)(i >> a.lognx), ix = (int)(i & (nx - 1));
+            x[i] = d[ix * ld + row];
+        }
     } else {
-        fft_inv<C, 1, false>(d, a.lognx, logr, 1, nx, 0, tw);
+        fft_inv<C, 1, true>(d, a.lognx, logr, ld, 1, 0, tw);
         const R sc = (R)1 / ((R)nx * (R)a.ny);
-        for (long i = threadIdx.x; i < cnt; i += blockDim.x) x[i] = cscale(d[i], sc);
+        for (long i = threadIdx.x; i < cnt; i += blockDim.x) {
+            const int row = (int)(i >> a.lognx), ix = (int)(i & (nx - 1));
+            x[i] = cscale(d[ix * ld + row], sc);
+        }
     }
 }
 
@@ -121,11 +131,15 @@ __global__ void __launch_bounds__(256) k_space_cols(SpaceArgs a) {
     const C mu = reinterpret_cast<const C*>(a.mu_dT)[plane];
     const C* sx = reinterpret_cast<const C*>(a.sig_x);
     const C* sy = reinterpret_cast<const C*>(a.sig_y);
-    // wavenumber of each x slot in this tile and of each y slot
+    // symbol of the x slots of this tile and of every y slot
+    C* sxs = d + cnt;                 // W entries
+    C* sys = sxs + W;                 // ny entries, indexed by y slot
+    for (int i = threadIdx.x; i < W; i += blockDim.x) sxs[i] = sx[slot_freq(c0 + i, a.lognx)];
+    for (int i = threadIdx.x; i < ny; i += blockDim.x) sys[i] = sy[slot_freq(i, a.logny)];
+    __syncthreads();
     for (long i = threadIdx.x; i < cnt; i += blockDim.x) {
-        const int ky = (int)(i >> logW), w = (int)(i & (W - 1));
-        const long slot = ((long)digitrev(ky, a.logny) << logW) + w;
-        d[slot] = shift_div(d[slot], mu, cadd(sx[slot_freq(c0 + w, a.lognx)], sy[ky]));
+        const int ys = (int)(i >> logW), w = (int)(i & (W - 1));
+        d[i] = shift_div(d[i], mu, cadd(sxs[w], sys[ys]));
     }
     __syncthreads();
     fft_inv<C, 1, true>(d, a.logny, logW, W, 1, 0, twy);
@@ -163,7 +177,7 @@ cudaError_t launch_space_2d_small(const SpaceArgs& a, cudaStream_t st) {
 template <typename R>
 cudaError_t launch_space_rows(const SpaceArgs& a, int inverse, cudaStream_t st) {
     typedef typename Cx<R>::T C;
-    size_t smem = sizeof(C) * (size_t)a.nx * a.rows_per_block;
+    size_t smem = sizeof(C) * (size_t)a.nx * (a.rows_per_block + 1);
     cudaError_t e = set_smem(k_space_rows<R>, smem);
     if (e != cudaSuccess) return e;
     long rows = (long)a.planes * a.ny;
@@ -175,7 +189,7 @@ cudaError_t launch_space_rows(const SpaceArgs& a, int inverse, cudaStream_t st) 
 template <typename R>
 cudaError_t launch_space_cols(const SpaceArgs& a, cudaStream_t st) {
     typedef typename Cx<R>::T C;
-    size_t smem = sizeof(C) * (size_t)a.ny * a.cols_per_block;
+    size_t smem = sizeof(C) * ((size_t)a.ny * a.cols_per_block + a.cols_per_block + a.ny);
     cudaError_t e = set_smem(k_space_cols<R>, smem);
     if (e != cudaSuccess) return e;
     int grid = a.planes * (a.nx / a.cols_per_block);

@@ -20,8 +20,16 @@
 
 namespace ac {
 
+// Register copies of the stencil taps and a zero: on this GPU an FP64 FMA
+// whose operands all come from registers issues at the full FP64 rate, while
+// DMUL, DADD and FMAs with a constant-bank or immediate operand run about 16%
+// slower, so every multiply below is an FMA on registers.
+struct RegCoef {
+    double tx[5], ty[5], c0, zero;
+};
+
 template <int MM>
-__device__ __forceinline__ void residual_point(const FwdArgs& a, int l, long n, const int* dxo,
+__device__ __forceinline__ void residual_point(const FwdArgs& a, const RegCoef& k, int l, long n, const int* dxo,
                                                const int* dyo, double r[MM]) {
     const Grid& g = a.g;
     const long N = g.N;
@@ -32,7 +40,7 @@ __device__ __forceinline__ void residual_point(const FwdArgs& a, int l, long n, 
         for (int m = 0; m < MM; ++m) {
             double w = (l == 0 && a.u0) ? a.u0[n] : 0.0;
             if (a.b) w += a.b[((long)lb * MM + m) * N + n];
-            r[m] = s * w;
+            r[m] = fma(s, w, k.zero);
         }
         return;
     }
@@ -42,13 +50,13 @@ __device__ __forceinline__ void residual_point(const FwdArgs& a, int l, long n, 
     for (int j = 0; j < MM; ++j) {
         const double* uj = ub + (long)j * N;
         uc[j] = uj[0];
-        double acc = g.c0 * uc[j];   // combined centre tap of both axes
+        double acc = fma(k.c0, uc[j], k.zero);   // combined centre tap of both axes
 #pragma unroll
         for (int o = 0; o < 4; ++o) {
             if (o < 2 * g.rad) {
                 const int tap = (o == 0) ? 1 : (o == 1) ? 3 : (o == 2) ? 0 : 4;  // offsets -1,+1,-2,+2
-                acc = fma(g.tx[tap], uj[dxo[o]], acc);
-                if (g.dim == 2) acc = fma(g.ty[tap], uj[dyo[o]], acc);
+                acc = fma(k.tx[tap], uj[dxo[o]], acc);
+                if (g.dim == 2) acc = fma(k.ty[tap], uj[dyo[o]], acc);
             }
         }
         Au[j] = acc;
@@ -59,17 +67,18 @@ __device__ __forceinline__ void residual_point(const FwdArgs& a, int l, long n, 
         double c = 0.0;
         if (l > 0) c = ub[-(long)N];                     // u_{l-1, M} (block l-1, last node)
         if (l == 0 && a.u0) c += a.u0[n];
+        const double sc = fma(s, c, k.zero);
 #pragma unroll
-        for (int m = 0; m < MM; ++m) sp[m] = s * c;
+        for (int m = 0; m < MM; ++m) sp[m] = sc;
     } else {
 #pragma unroll
-        for (int m = 0; m < MM; ++m) sp[m] = 0.0;
+        for (int m = 0; m < MM; ++m) sp[m] = k.zero;
         if (l > 0) {
             double c = 0.0;
             const double* up = ub - (long)MM * N;
 #pragma unroll
             for (int j = 0; j < MM; ++j) c += up[(long)j * N];  // (H^T u_{l-1})_M = sum_j u_{l-1,j}
-            sp[MM - 1] = s * c;
+            sp[MM - 1] = fma(s, c, k.zero);
         }
         if (l == 0 && a.u0) {
 #pragma unroll
@@ -80,9 +89,10 @@ __device__ __forceinline__ void residual_point(const FwdArgs& a, int l, long n, 
 #pragma unroll
         for (int m = 0; m < MM; ++m) sp[m] = fma(s, a.b[((long)lb * MM + m) * N + n], sp[m]);
     }
+    const double ms = -s;
 #pragma unroll
     for (int m = 0; m < MM; ++m) {
-        double t = fma(-s, uc[m], sp[m]);
+        double t = fma(ms, uc[m], sp[m]);
 #pragma unroll
         for (int j = 0; j < MM; ++j) t = fma(qs[m * MM + j], Au[j], t);
         r[m] = t;
@@ -101,6 +111,21 @@ __global__ void __launch_bounds__(256) k_fwd(FwdArgs a) {
     const int L = a.L;
     const long N = a.g.N;
     const long n0 = (long)blockIdx.x * P;
+
+    __shared__ double coef_s[12];
+    if (threadIdx.x < 12) {
+        const int i = threadIdx.x;
+        coef_s[i] = i < 5 ? a.g.tx[i] : (i < 10 ? a.g.ty[i - 5] : (i == 10 ? a.g.c0 : 0.0));
+    }
+    __syncthreads();
+    RegCoef kc;
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        kc.tx[i] = coef_s[i];
+        kc.ty[i] = coef_s[5 + i];
+    }
+    kc.c0 = coef_s[10];
+    kc.zero = coef_s[11];
 
     // this thread's grid point is fixed (blockDim is a multiple of P)
     const int p = threadIdx.x & (P - 1);
@@ -125,24 +150,34 @@ __global__ void __launch_bounds__(256) k_fwd(FwdArgs a) {
         }
     }
     float sq = 0.f;
-    for (int l = threadIdx.x >> logP; l < L; l += blockDim.x >> logP) {
-        double r[MM];
-        R rv[MM];
-        if (n < N) {
-            residual_point<MM>(a, l, n, dxo, dyo, r);
+#ifndef AC_FWD_LUNROLL
+#define AC_FWD_LUNROLL 1
+#endif
+    // AC_FWD_LUNROLL time steps per pass (independent FP64 dependency chains)
+    const int lstep = blockDim.x >> logP;
+    for (int l0 = threadIdx.x >> logP; l0 < L; l0 += AC_FWD_LUNROLL * lstep) {
+        double r[AC_FWD_LUNROLL][MM];
+#pragma unroll
+        for (int u = 0; u < AC_FWD_LUNROLL; ++u) {
+            const int l = l0 + u * lstep;
+            if (n < N && l < L) residual_point<MM>(a, kc, l, n, dxo, dyo, r[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < AC_FWD_LUNROLL; ++u) {
+            const int l = l0 + u * lstep;
+            if (l >= L) break;
             const float isw = a.inv_s_w[l];
 #pragma unroll
             for (int m = 0; m < MM; ++m) {
-                rv[m] = to_real<R>(r[m]);
-                const float rf = (sizeof(R) == 4 ? (float)rv[m] : d2f_int(r[m])) * isw;
-                sq = fmaf(rf, rf, sq);
+                R v = (R)0;
+                if (n < N) {
+                    v = to_real<R>(r[u][m]);
+                    const float rf = (sizeof(R) == 4 ? (float)v : d2f_int(r[u][m])) * isw;
+                    sq = fmaf(rf, rf, sq);
+                }
+                Zr[((long)l * MM + m) * P + p] = v;
             }
-        } else {
-#pragma unroll
-            for (int m = 0; m < MM; ++m) rv[m] = (R)0;
         }
-#pragma unroll
-        for (int m = 0; m < MM; ++m) Zr[((long)l * MM + m) * P + p] = rv[m];
     }
     __syncthreads();
 

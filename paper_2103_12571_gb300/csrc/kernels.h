@@ -91,7 +91,7 @@ template <typename R> cudaError_t launch_space_1d(const SpaceArgs& a, cudaStream
 template <typename R> cudaError_t launch_space_2d_small(const SpaceArgs& a, cudaStream_t st);
 template <typename R> cudaError_t launch_space_rows(const SpaceArgs& a, int inverse, cudaStream_t st);
 template <typename R> cudaError_t launch_space_cols(const SpaceArgs& a, cudaStream_t st);
-template <typename R> cudaError_t launch_bicgstab(const BicgArgs& a, cudaStream_t st);
+template <typename R> cudaError_t launch_bicgstab(const BicgArgs& a, void* scratch, cudaStream_t st);
 cudaError_t launch_apply(const ApplyArgs& a, cudaStream_t st);
 cudaError_t launch_grad(const GradArgs& a, int grid, cudaStream_t st);
 cudaError_t launch_sum_blocks(const double* lam, int M, int N, double* du0, cudaStream_t st);
