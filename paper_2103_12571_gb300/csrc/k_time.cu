@@ -28,7 +28,9 @@ struct RegCoef {
     double tx[5], ty[5], c0, zero;
 };
 
-template <int MM>
+// RAD (stencil radius) and DIM are compile-time: FP64 instructions that a
+// runtime test predicates off still occupy the FP64 pipe of this GPU.
+template <int MM, int RAD, int DIM>
 __device__ __forceinline__ void residual_point(const FwdArgs& a, const RegCoef& k, int l, long n, const int* dxo,
                                                const int* dyo, double r[MM]) {
     const Grid& g = a.g;
@@ -52,12 +54,10 @@ __device__ __forceinline__ void residual_point(const FwdArgs& a, const RegCoef& 
         uc[j] = uj[0];
         double acc = fma(k.c0, uc[j], k.zero);   // combined centre tap of both axes
 #pragma unroll
-        for (int o = 0; o < 4; ++o) {
-            if (o < 2 * g.rad) {
-                const int tap = (o == 0) ? 1 : (o == 1) ? 3 : (o == 2) ? 0 : 4;  // offsets -1,+1,-2,+2
-                acc = fma(k.tx[tap], uj[dxo[o]], acc);
-                if (g.dim == 2) acc = fma(k.ty[tap], uj[dyo[o]], acc);
-            }
+        for (int o = 0; o < 2 * RAD; ++o) {
+            const int tap = (o == 0) ? 1 : (o == 1) ? 3 : (o == 2) ? 0 : 4;  // offsets -1,+1,-2,+2
+            acc = fma(k.tx[tap], uj[dxo[o]], acc);
+            if (DIM == 2) acc = fma(k.ty[tap], uj[dyo[o]], acc);
         }
         Au[j] = acc;
     }
@@ -99,7 +99,7 @@ __device__ __forceinline__ void residual_point(const FwdArgs& a, const RegCoef& 
     }
 }
 
-template <typename R, int MM>
+template <typename R, int MM, int RAD, int DIM>
 __global__ void __launch_bounds__(256) k_fwd(FwdArgs a) {
     typedef typename Cx<R>::T C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(256) k_fwd(FwdArgs a) {
 #pragma unroll
         for (int u = 0; u < AC_FWD_LUNROLL; ++u) {
             const int l = l0 + u * lstep;
-            if (n < N && l < L) residual_point<MM>(a, kc, l, n, dxo, dyo, r[u]);
+            if (n < N && l < L) residual_point<MM, RAD, DIM>(a, kc, l, n, dxo, dyo, r[u]);
         }
 #pragma unroll
         for (int u = 0; u < AC_FWD_LUNROLL; ++u) {
@@ -295,20 +295,33 @@ __global__ void __launch_bounds__(256) k_upd(UpdArgs a) {
     if (threadIdx.x == 0) a.part[blockIdx.x] = tot;
 }
 
+template <typename R, int MM, int RAD, int DIM>
+static cudaError_t launch_fwd_t(const FwdArgs& a, int grid, size_t smem, cudaStream_t st) {
+    cudaError_t e = cudaFuncSetAttribute(k_fwd<R, MM, RAD, DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    k_fwd<R, MM, RAD, DIM><<<grid, 256, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename R, int MM>
+static cudaError_t launch_fwd_m(const FwdArgs& a, int grid, size_t smem, cudaStream_t st) {
+    const int key = (a.g.rad == 2 ? 2 : 0) + (a.g.dim == 2 ? 1 : 0);
+    switch (key) {
+        case 0: return launch_fwd_t<R, MM, 1, 1>(a, grid, smem, st);
+        case 1: return launch_fwd_t<R, MM, 1, 2>(a, grid, smem, st);
+        case 2: return launch_fwd_t<R, MM, 2, 1>(a, grid, smem, st);
+        default: return launch_fwd_t<R, MM, 2, 2>(a, grid, smem, st);
+    }
+}
+
 template <typename R>
 cudaError_t launch_fwd(const FwdArgs& a, int grid, size_t smem, cudaStream_t st) {
     switch (a.M) {
-#define AC_CASE(MMV)                                                                          \
-    case MMV: {                                                                               \
-        cudaError_t e = cudaFuncSetAttribute(k_fwd<R, MMV>,                                   \
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,     \
-                                             (int)smem);                                      \
-        if (e != cudaSuccess) return e;                                                       \
-        k_fwd<R, MMV><<<grid, 256, smem, st>>>(a);                                            \
-        return cudaGetLastError();                                                            \
-    }
-        AC_CASE(1) AC_CASE(2) AC_CASE(3) AC_CASE(4)
-#undef AC_CASE
+        case 1: return launch_fwd_m<R, 1>(a, grid, smem, st);
+        case 2: return launch_fwd_m<R, 2>(a, grid, smem, st);
+        case 3: return launch_fwd_m<R, 3>(a, grid, smem, st);
+        case 4: return launch_fwd_m<R, 4>(a, grid, smem, st);
     }
     return cudaErrorInvalidValue;
 }
