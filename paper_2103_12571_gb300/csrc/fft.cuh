@@ -135,12 +135,14 @@ __device__ __forceinline__ void fft_stage(C* data, int logn, int logns, int logb
         C w[R];
 #pragma unroll
         for (int r = 1; r < R; ++r) w[r] = tw[(j * r) << twshift];
-        C* p = data + (long)base * js + (long)b * bs;
+        // shared-memory offsets fit in 32 bits
+        C* p = data + (base * js + b * bs);
+        const int mjs = m * js;
 #pragma unroll
         for (int mm = 0; mm < MI; ++mm) {
             C v[R];
 #pragma unroll
-            for (int r = 0; r < R; ++r) v[r] = p[(long)r * m * js + mm * ms];
+            for (int r = 0; r < R; ++r) v[r] = p[r * mjs + mm * ms];
             if (!INV) {
                 small_dft<R, false>(v);
 #pragma unroll
@@ -151,7 +153,7 @@ __device__ __forceinline__ void fft_stage(C* data, int logn, int logns, int logb
                 small_dft<R, true>(v);
             }
 #pragma unroll
-            for (int r = 0; r < R; ++r) p[(long)r * m * js + mm * ms] = v[r];
+            for (int r = 0; r < R; ++r) p[r * mjs + mm * ms] = v[r];
         }
     }
     __syncthreads();

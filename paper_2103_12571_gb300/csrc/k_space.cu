@@ -11,13 +11,18 @@
 
 namespace ac {
 
+// v / (1 - mu * sig): multiply by conj(den) / |den|^2 with one reciprocal
+// (|den| >= 1 here whenever Re(mu sig) <= 0, so no scaling is needed)
+__device__ __forceinline__ float rcp_c64(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double rcp_c64(double x) { return 1.0 / x; }
+
 template <typename C>
 __device__ __forceinline__ C shift_div(C v, C mu, C sig) {
-    // v / (1 - mu * sig)
     C den = cmul(mu, sig);
     den.x = (decltype(den.x))1 - den.x;
     den.y = -den.y;
-    return cdiv(v, den);
+    const auto inv = rcp_c64(den.x * den.x + den.y * den.y);
+    return cscale(cmulc(v, den), inv);
 }
 
 // One CTA per 1D plane held in shared memory.

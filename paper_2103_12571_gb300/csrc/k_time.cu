@@ -267,6 +267,7 @@ __global__ void __launch_bounds__(256) k_upd(UpdArgs a) {
 
     float emax = 0.f;
     const bool pairs = (N & 1) == 0;
+#pragma unroll 4
     for (int idx = threadIdx.x; idx < L * MM * HP; idx += blockDim.x) {
         const int q = idx & (HP - 1);
         const int lm = idx >> logHP;
