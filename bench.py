@@ -97,6 +97,61 @@ def fp64_flops_per_dof(M, taps):
     return (1 + 2 * (taps - 1)) + 2 * M + 2 + 1.0 / M
 
 
+KERNEL_SOURCES = ["paper_2103_12571_gb300/csrc/k_time.cu", "paper_2103_12571_gb300/csrc/fft.cuh",
+                  "paper_2103_12571_gb300/csrc/common.cuh", "paper_2103_12571_gb300/csrc/k_space.cu"]
+
+
+def source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the last ncu capture, if it was
+    taken on the current kernel sources (else None)."""
+    try:
+        t = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+    except (OSError, ValueError):
+        return None
+    if t.get("source_sha256") != source_hash():
+        return None
+    return t.get("kernels", {}).get(kernel)
+
+
+def roofline(dom, dom_ms, D, L, M, N):
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    # FP64 pipe: 2 DFMA/clk/SM (a probe reached 98% of it) x 152 SMs x 2.07 GHz x 2 flop
+    fp64_peak = 2 * 2 * 152 * 2.07e9 / 1e12
+    csz = 8
+    F = L // 2 + 1
+    if dom == "resid_tfft_mix":
+        flops = fp64_flops_per_dof(M, 5) * D
+        roof = {"bound": "alu", "achieved": flops / (dom_ms * 1e-3) / 1e12, "peak": fp64_peak, "unit": "TFLOP/s",
+                "peak_source": "derived: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz x 2 flop (FP64 pipe)",
+                "algorithmic_flops_per_launch": flops,
+                "hbm_gbs_algorithmic": (8.0 * D + F * M * N * csz) / (dom_ms * 1e-3) / 1e9}
+    else:
+        bytes_ = {"spatial_solve": 6 * F * M * N * csz,
+                  "mix_tifft_update": F * M * N * csz + 16.0 * D}.get(dom, 16.0 * D)
+        roof = {"bound": "hbm", "achieved": bytes_ / (dom_ms * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)", "algorithmic_bytes_per_launch": bytes_}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["kernel"] = dom
+    roof["kernel_ms"] = dom_ms
+    tr = measured_traffic({"resid_tfft_mix": "k_fwd", "spatial_solve": "k_space", "mix_tifft_update": "k_upd"}.get(dom, dom))
+    roof["traffic"] = tr
+    return roof
+
+
 def run_ours(args):
     import torch
     from paper_2103_12571_gb300 import workloads
@@ -151,6 +206,12 @@ def run_ours(args):
         ms = float(t.item())
     value = D * world / (ms * 1e-3)
 
+    if args.no_extras:
+        if rank == 0:
+            print(json.dumps({"metric": "space-time DoF*iterations/s", "value": value, "unit": "DoF*it/s",
+                              "ms_per_step": ms, "steps": args.steps, "warmup": args.warmup,
+                              "kernels_ms_per_step": {k: v[0] / args.steps for k, v in prof.items() if v[1]}}))
+        return
     # ---- end to end through the public API: pinned host u0 -> device, one
     # iteration with its residual norm read back to the host
     u0_host = torch.from_numpy(u0_np).pin_memory()
@@ -189,32 +250,9 @@ def run_ours(args):
 
     # ---- roofline of the dominant kernel
     kern = {k: v for k, v in prof.items() if v[1] > 0}
-    total_ms = sum(v[0] for v in kern.values())
     dom = max(kern, key=lambda k: kern[k][0])
     dom_ms = kern[dom][0] / kern[dom][1]
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except (OSError, ValueError):
-        pass
-    hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    fp64_peak = 2 * 2 * 152 * 2.07e9 / 1e12  # 2 DFMA/clk/SM x 152 SMs x 2.07 GHz x 2 flop
-    csz = 8
-    F = L // 2 + 1
-    if dom == "resid_tfft_mix":
-        flops = fp64_flops_per_dof(M, 5) * D
-        roof = {"bound": "alu", "achieved": flops / (dom_ms * 1e-3) / 1e12, "peak": fp64_peak,
-                "unit": "TFLOP/s", "peak_kind": "FP64 FMA pipe, 2/clk/SM at 2.07 GHz (derived)"}
-        roof["frac"] = roof["achieved"] / roof["peak"]
-        roof["hbm_gbs_algorithmic"] = (8.0 * D + F * M * N * csz) / (dom_ms * 1e-3) / 1e9
-    else:
-        bytes_ = {"spatial_solve": 6 * F * M * N * csz,
-                  "mix_tifft_update": F * M * N * csz + 16.0 * D}.get(dom, 16.0 * D)
-        roof = {"bound": "hbm", "achieved": bytes_ / (dom_ms * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s"}
-        roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["kernel"] = dom
-    roof["kernel_ms"] = dom_ms
-    roof["traffic"] = None
+    roof = roofline(dom, dom_ms, D, L, M, N)
     out = {
         "metric": "space-time DoF*iterations/s (one alpha-circulant Richardson iteration, mixed FP64/c64)",
         "value": value, "unit": "DoF*it/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -322,6 +360,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-samples", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="only the timed steps (used for ncu captures): no e2e, time-to-tolerance or CPU legs")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
