@@ -462,7 +462,7 @@ static int richardson_loop(ac_plan* p, const double* u0, const double* b, int b_
     // Lipschitz estimate) when the caller gives none; for a zero initial
     // iterate (adjoint) the bound L ||w||_inf
     double m = sc.m0;
-    if (!(m > 0)) {
+    if (sc.mode == AC_ALPHA_PAPER && !(m > 0)) {
         if (u0) {
             double au0 = 0.0;
             rc = a_u0_inf(p, u0, transposed, &au0, st);
@@ -727,7 +727,7 @@ int ac_setup(const ac_problem* prob, int M, int L, double dT, const ac_alpha_sch
     if (e == cudaSuccess) e = cudaMallocHost((void**)&p->h_part_upd, sizeof(float) * p->grid);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&p->h_part_d, sizeof(double) * p->part_d_len);
     if (e == cudaSuccess && p->spatial_path == 3) e = cudaMallocHost((void**)&p->h_iters, sizeof(int) * F * M);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_res, cudaEventBlockingSync);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_res, cudaEventDisableTiming);  // spin: low latency
     if (e != cudaSuccess) {
         int rc = fail(AC_ERR_CUDA, "allocation failed: %s", cudaGetErrorString(e));
         ac_destroy(p);

@@ -16,19 +16,25 @@
 
 namespace ac {
 
-// stage plan: radix 8 while at least 3 bits remain, then one radix 4 or 2
-__host__ __device__ __forceinline__ int fft_nstages(int logn) { return (logn + 2) / 3; }
+// Stage plan of a length-2^logn transform with radices up to 2^MAXB: full
+// stages of MAXB bits while at least MAXB bits remain, then one stage with
+// the rest.  The time transforms use MAXB = 3 (radix 8), the spatial ones
+// MAXB = 4 (radix 16).  Forward and inverse of one length must use the same plan.
+template <int MAXB>
+__host__ __device__ __forceinline__ int fft_nstages(int logn) { return (logn + MAXB - 1) / MAXB; }
+template <int MAXB>
 __host__ __device__ __forceinline__ int fft_stage_bits(int logn, int s) {
-    const int full = logn / 3;
-    return s < full ? 3 : logn - 3 * full;
+    const int full = logn / MAXB;
+    return s < full ? MAXB : logn - MAXB * full;
 }
 
 // slot of frequency k after the forward transform (and input slot of the inverse)
+template <int MAXB>
 __host__ __device__ __forceinline__ int digitrev(int k, int logn) {
     int p = 0, used = 0;
-    const int ns = fft_nstages(logn);
+    const int ns = fft_nstages<MAXB>(logn);
     for (int s = 0; s < ns; ++s) {
-        const int b = fft_stage_bits(logn, s);
+        const int b = fft_stage_bits<MAXB>(logn, s);
         used += b;
         p |= (k & ((1 << b) - 1)) << (logn - used);
         k >>= b;
@@ -37,11 +43,12 @@ __host__ __device__ __forceinline__ int digitrev(int k, int logn) {
 }
 
 // frequency held by slot p (inverse of digitrev)
+template <int MAXB>
 __host__ __device__ __forceinline__ int slot_freq(int p, int logn) {
     int k = 0, used = 0, shift = 0;
-    const int ns = fft_nstages(logn);
+    const int ns = fft_nstages<MAXB>(logn);
     for (int s = 0; s < ns; ++s) {
-        const int b = fft_stage_bits(logn, s);
+        const int b = fft_stage_bits<MAXB>(logn, s);
         used += b;
         k |= ((p >> (logn - used)) & ((1 << b) - 1)) << shift;
         shift += b;
@@ -112,10 +119,10 @@ __device__ __forceinline__ void small_dft(C* v) {
 // One stage over all batches.  Element (j, b, mm) lives at
 // data[j * js + b * bs + mm * ms]; b < 2^logb; mm < MI is looped per thread.
 // BFAST: consecutive threads take consecutive b (else consecutive j).
-template <typename C, int R, int MI, bool INV, bool BFAST>
+template <typename C, int R, int MI, bool INV, bool BFAST, bool UNIT>
 __device__ __forceinline__ void fft_stage(C* data, int logn, int logns, int logb, int js, int bs, int ms,
                                           const C* __restrict__ tw) {
-    constexpr int logR = R == 8 ? 3 : (R == 4 ? 2 : 1);
+    constexpr int logR = R == 16 ? 4 : (R == 8 ? 3 : (R == 4 ? 2 : 1));
     const int logm = logns - logR;
     const int m = 1 << logm;
     const int logitems_b = logn - logR;  // items per batch
@@ -133,8 +140,10 @@ __device__ __forceinline__ void fft_stage(C* data, int logn, int logns, int logb
         const int j = i & (m - 1);
         const int base = ((i >> logm) << logns) + j;
         C w[R];
+        if (!UNIT) {
 #pragma unroll
-        for (int r = 1; r < R; ++r) w[r] = tw[(j * r) << twshift];
+            for (int r = 1; r < R; ++r) w[r] = tw[(j * r) << twshift];
+        }
         // shared-memory offsets fit in 32 bits
         C* p = data + (base * js + b * bs);
         const int mjs = m * js;
@@ -145,11 +154,15 @@ __device__ __forceinline__ void fft_stage(C* data, int logn, int logns, int logb
             for (int r = 0; r < R; ++r) v[r] = p[r * mjs + mm * ms];
             if (!INV) {
                 small_dft<R, false>(v);
+                if (!UNIT) {
 #pragma unroll
-                for (int r = 1; r < R; ++r) v[r] = cmul(v[r], w[r]);
+                    for (int r = 1; r < R; ++r) v[r] = cmul(v[r], w[r]);
+                }
             } else {
+                if (!UNIT) {
 #pragma unroll
-                for (int r = 1; r < R; ++r) v[r] = cmulc(v[r], w[r]);
+                    for (int r = 1; r < R; ++r) v[r] = cmulc(v[r], w[r]);
+                }
                 small_dft<R, true>(v);
             }
 #pragma unroll
@@ -159,36 +172,42 @@ __device__ __forceinline__ void fft_stage(C* data, int logn, int logns, int logb
     __syncthreads();
 }
 
-// Forward transform of length 2^logn (tw: 2^logn entries w_n^k).  Ends with
-// __syncthreads(); callers must synchronise before it.
-template <typename C, int MI, bool BFAST>
+// radix dispatch; only radices up to 2^MAXB are instantiated (a radix-16
+// stage that is never taken would still raise the kernel's register count)
+template <typename C, int MI, bool INV, bool BFAST, bool UNIT, int MAXB>
+__device__ __forceinline__ void fft_stage_r(int bits, C* data, int logn, int logns, int logb, int js, int bs, int ms,
+                                            const C* __restrict__ tw) {
+    if (MAXB >= 4 && bits == 4)
+        fft_stage<C, (MAXB >= 4 ? 16 : 8), MI, INV, BFAST, UNIT>(data, logn, logns, logb, js, bs, ms, tw);
+    else if (bits == 3) fft_stage<C, 8, MI, INV, BFAST, UNIT>(data, logn, logns, logb, js, bs, ms, tw);
+    else if (bits == 2) fft_stage<C, 4, MI, INV, BFAST, UNIT>(data, logn, logns, logb, js, bs, ms, tw);
+    else fft_stage<C, 2, MI, INV, BFAST, UNIT>(data, logn, logns, logb, js, bs, ms, tw);
+}
+
+// Forward transform of length 2^logn (tw: 2^logn entries w_n^k), radices up
+// to 2^MAXB.  Ends with __syncthreads(); callers must synchronise before it.
+// The last stage has unit twiddles (its blocks have one column).
+template <typename C, int MI, bool BFAST, int MAXB = 3>
 __device__ void fft_fwd(C* data, int logn, int logb, int js, int bs, int ms, const C* __restrict__ tw) {
-    const int ns = fft_nstages(logn);
+    const int ns = fft_nstages<MAXB>(logn);
     int logns = logn;
     for (int s = 0; s < ns; ++s) {
-        const int bits = fft_stage_bits(logn, s);
-        if (bits == 3) fft_stage<C, 8, MI, false, BFAST>(data, logn, logns, logb, js, bs, ms, tw);
-        else if (bits == 2) fft_stage<C, 4, MI, false, BFAST>(data, logn, logns, logb, js, bs, ms, tw);
-        else fft_stage<C, 2, MI, false, BFAST>(data, logn, logns, logb, js, bs, ms, tw);
+        const int bits = fft_stage_bits<MAXB>(logn, s);
+        if (s == ns - 1) fft_stage_r<C, MI, false, BFAST, true, MAXB>(bits, data, logn, logns, logb, js, bs, ms, tw);
+        else fft_stage_r<C, MI, false, BFAST, false, MAXB>(bits, data, logn, logns, logb, js, bs, ms, tw);
         logns -= bits;
     }
 }
 
 // Inverse (unnormalised) transform: digit-reversed order in, natural out.
-template <typename C, int MI, bool BFAST>
+template <typename C, int MI, bool BFAST, int MAXB = 3>
 __device__ void fft_inv(C* data, int logn, int logb, int js, int bs, int ms, const C* __restrict__ tw) {
-    const int ns = fft_nstages(logn);
-    int logns = logn;
-    int lns[8];
-    for (int s = 0; s < ns; ++s) {
-        lns[s] = logns;
-        logns -= fft_stage_bits(logn, s);
-    }
+    const int ns = fft_nstages<MAXB>(logn);
     for (int s = ns - 1; s >= 0; --s) {
-        const int bits = fft_stage_bits(logn, s);
-        if (bits == 3) fft_stage<C, 8, MI, true, BFAST>(data, logn, lns[s], logb, js, bs, ms, tw);
-        else if (bits == 2) fft_stage<C, 4, MI, true, BFAST>(data, logn, lns[s], logb, js, bs, ms, tw);
-        else fft_stage<C, 2, MI, true, BFAST>(data, logn, lns[s], logb, js, bs, ms, tw);
+        const int bits = fft_stage_bits<MAXB>(logn, s);
+        const int logns = logn - MAXB * s;   // block size entering DIF stage s (all earlier stages are full)
+        if (s == ns - 1) fft_stage_r<C, MI, true, BFAST, true, MAXB>(bits, data, logn, logns, logb, js, bs, ms, tw);
+        else fft_stage_r<C, MI, true, BFAST, false, MAXB>(bits, data, logn, logns, logb, js, bs, ms, tw);
     }
 }
 

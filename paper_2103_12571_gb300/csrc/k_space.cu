@@ -29,6 +29,7 @@ __device__ __forceinline__ C shift_div(C v, C mu, C sig) {
 template <typename R>
 __global__ void __launch_bounds__(512) k_space_1d(SpaceArgs a) {
     typedef typename Cx<R>::T C;
+    constexpr int SB = sizeof(R) == 8 ? 4 : 3;   // radix 16 in FP64, radix 8 in FP32 (register pressure)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* d = reinterpret_cast<C*>(smem_raw);
     const int n = a.nx, logn = a.lognx;
@@ -36,12 +37,12 @@ __global__ void __launch_bounds__(512) k_space_1d(SpaceArgs a) {
     for (int i = threadIdx.x; i < n; i += blockDim.x) d[i] = x[i];
     __syncthreads();
     const C* tw = reinterpret_cast<const C*>(a.tw_x);
-    fft_fwd<C, 1, false>(d, logn, 0, 1, 0, 0, tw);
+    fft_fwd<C, 1, false, SB>(d, logn, 0, 1, 0, 0, tw);
     const C mu = reinterpret_cast<const C*>(a.mu_dT)[blockIdx.x];
     const C* sig = reinterpret_cast<const C*>(a.sig_x);
-    for (int i = threadIdx.x; i < n; i += blockDim.x) d[digitrev(i, logn)] = shift_div(d[digitrev(i, logn)], mu, sig[i]);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) d[digitrev<SB>(i, logn)] = shift_div(d[digitrev<SB>(i, logn)], mu, sig[i]);
     __syncthreads();
-    fft_inv<C, 1, false>(d, logn, 0, 1, 0, 0, tw);
+    fft_inv<C, 1, false, SB>(d, logn, 0, 1, 0, 0, tw);
     const R sc = (R)1 / (R)n;
     for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] = cscale(d[i], sc);
 }
@@ -51,6 +52,7 @@ __global__ void __launch_bounds__(512) k_space_1d(SpaceArgs a) {
 template <typename R>
 __global__ void __launch_bounds__(512) k_space_2d_small(SpaceArgs a) {
     typedef typename Cx<R>::T C;
+    constexpr int SB = sizeof(R) == 8 ? 4 : 3;   // radix 16 in FP64, radix 8 in FP32 (register pressure)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* d = reinterpret_cast<C*>(smem_raw);
     const int nx = a.nx, ny = a.ny, lx = a.lognx, ly = a.logny;
@@ -60,19 +62,19 @@ __global__ void __launch_bounds__(512) k_space_2d_small(SpaceArgs a) {
     __syncthreads();
     const C* twx = reinterpret_cast<const C*>(a.tw_x);
     const C* twy = reinterpret_cast<const C*>(a.tw_y);
-    fft_fwd<C, 1, false>(d, lx, ly, 1, nx, 0, twx);   // rows (x index fastest across threads)
-    fft_fwd<C, 1, true>(d, ly, lx, nx, 1, 0, twy);    // columns (column index fastest)
+    fft_fwd<C, 1, false, SB>(d, lx, ly, 1, nx, 0, twx);   // rows (x index fastest across threads)
+    fft_fwd<C, 1, true, SB>(d, ly, lx, nx, 1, 0, twy);    // columns (column index fastest)
     const C mu = reinterpret_cast<const C*>(a.mu_dT)[blockIdx.x];
     const C* sx = reinterpret_cast<const C*>(a.sig_x);
     const C* sy = reinterpret_cast<const C*>(a.sig_y);
     for (long i = threadIdx.x; i < N; i += blockDim.x) {
         const int ky = (int)(i >> lx), kx = (int)(i & (nx - 1));
-        const long slot = ((long)digitrev(ky, ly) << lx) + digitrev(kx, lx);
+        const long slot = ((long)digitrev<SB>(ky, ly) << lx) + digitrev<SB>(kx, lx);
         d[slot] = shift_div(d[slot], mu, cadd(sx[kx], sy[ky]));
     }
     __syncthreads();
-    fft_inv<C, 1, true>(d, ly, lx, nx, 1, 0, twy);
-    fft_inv<C, 1, false>(d, lx, ly, 1, nx, 0, twx);
+    fft_inv<C, 1, true, SB>(d, ly, lx, nx, 1, 0, twy);
+    fft_inv<C, 1, false, SB>(d, lx, ly, 1, nx, 0, twx);
     const R sc = (R)1 / (R)N;
     for (long i = threadIdx.x; i < N; i += blockDim.x) x[i] = cscale(d[i], sc);
 }
@@ -82,6 +84,7 @@ __global__ void __launch_bounds__(512) k_space_2d_small(SpaceArgs a) {
 template <typename R>
 __global__ void __launch_bounds__(256) k_space_rows(SpaceArgs a, int inverse) {
     typedef typename Cx<R>::T C;
+    constexpr int SB = sizeof(R) == 8 ? 4 : 3;   // radix 16 in FP64, radix 8 in FP32 (register pressure)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* d = reinterpret_cast<C*>(smem_raw);
     const int nx = a.nx, rpb = a.rows_per_block;
@@ -97,13 +100,13 @@ __global__ void __launch_bounds__(256) k_space_rows(SpaceArgs a, int inverse) {
     __syncthreads();
     const C* tw = reinterpret_cast<const C*>(a.tw_x);
     if (!inverse) {
-        fft_fwd<C, 1, true>(d, a.lognx, logr, ld, 1, 0, tw);
+        fft_fwd<C, 1, true, SB>(d, a.lognx, logr, ld, 1, 0, tw);
         for (long i = threadIdx.x; i < cnt; i += blockDim.x) {
             const int row = (int)(i >> a.lognx), ix = (int)(i & (nx - 1));
             x[i] = d[ix * ld + row];
         }
     } else {
-        fft_inv<C, 1, true>(d, a.lognx, logr, ld, 1, 0, tw);
+        fft_inv<C, 1, true, SB>(d, a.lognx, logr, ld, 1, 0, tw);
         const R sc = (R)1 / ((R)nx * (R)a.ny);
         for (long i = threadIdx.x; i < cnt; i += blockDim.x) {
             const int row = (int)(i >> a.lognx), ix = (int)(i & (nx - 1));
@@ -117,6 +120,7 @@ __global__ void __launch_bounds__(256) k_space_rows(SpaceArgs a, int inverse) {
 template <typename R>
 __global__ void __launch_bounds__(256) k_space_cols(SpaceArgs a) {
     typedef typename Cx<R>::T C;
+    constexpr int SB = sizeof(R) == 8 ? 4 : 3;   // radix 16 in FP64, radix 8 in FP32 (register pressure)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* d = reinterpret_cast<C*>(smem_raw);
     const int nx = a.nx, ny = a.ny, W = a.cols_per_block;
@@ -132,22 +136,22 @@ __global__ void __launch_bounds__(256) k_space_cols(SpaceArgs a) {
     }
     __syncthreads();
     const C* twy = reinterpret_cast<const C*>(a.tw_y);
-    fft_fwd<C, 1, true>(d, a.logny, logW, W, 1, 0, twy);
+    fft_fwd<C, 1, true, SB>(d, a.logny, logW, W, 1, 0, twy);
     const C mu = reinterpret_cast<const C*>(a.mu_dT)[plane];
     const C* sx = reinterpret_cast<const C*>(a.sig_x);
     const C* sy = reinterpret_cast<const C*>(a.sig_y);
     // symbol of the x slots of this tile and of every y slot
     C* sxs = d + cnt;                 // W entries
     C* sys = sxs + W;                 // ny entries, indexed by y slot
-    for (int i = threadIdx.x; i < W; i += blockDim.x) sxs[i] = sx[slot_freq(c0 + i, a.lognx)];
-    for (int i = threadIdx.x; i < ny; i += blockDim.x) sys[i] = sy[slot_freq(i, a.logny)];
+    for (int i = threadIdx.x; i < W; i += blockDim.x) sxs[i] = sx[slot_freq<SB>(c0 + i, a.lognx)];
+    for (int i = threadIdx.x; i < ny; i += blockDim.x) sys[i] = sy[slot_freq<SB>(i, a.logny)];
     __syncthreads();
     for (long i = threadIdx.x; i < cnt; i += blockDim.x) {
         const int ys = (int)(i >> logW), w = (int)(i & (W - 1));
         d[i] = shift_div(d[i], mu, cadd(sxs[w], sys[ys]));
     }
     __syncthreads();
-    fft_inv<C, 1, true>(d, a.logny, logW, W, 1, 0, twy);
+    fft_inv<C, 1, true, SB>(d, a.logny, logW, W, 1, 0, twy);
     for (long i = threadIdx.x; i < cnt; i += blockDim.x) {
         const int iy = (int)(i >> logW), w = (int)(i & (W - 1));
         x[(long)iy * nx + w] = d[i];

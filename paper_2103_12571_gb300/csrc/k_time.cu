@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(256) k_fwd(FwdArgs a) {
     const R half = (R)0.5;
     for (int idx = threadIdx.x; idx < a.F * HP; idx += blockDim.x) {
         const int k = idx >> logHP, q = idx & (HP - 1);
-        const int pk = digitrev(k, a.logL), pn = digitrev((L - k) & (L - 1), a.logL);
+        const int pk = digitrev<3>(k, a.logL), pn = digitrev<3>((L - k) & (L - 1), a.logL);
         const bool realbin = (k == 0) || (2 * k == L);
         C A[MM], B[MM];
 #pragma unroll
@@ -245,7 +245,7 @@ __global__ void __launch_bounds__(256) k_upd(UpdArgs a) {
         }
         const C* Pk = Pm + (long)k * MM * MM;
         const bool realbin = (k == 0) || (2 * k == L);
-        const int pk = digitrev(k, a.logL), pn = digitrev((L - k) & (L - 1), a.logL);
+        const int pk = digitrev<3>(k, a.logL), pn = digitrev<3>((L - k) & (L - 1), a.logL);
 #pragma unroll
         for (int m = 0; m < MM; ++m) {
             C ya = cmake((R)0, (R)0), yb = ya;
