@@ -86,6 +86,25 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(value, world):
+    """Max of a per-rank float over all ranks (the job's step time); works
+    with the NCCL and gloo backends."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(dof_per_rank, ms_max, world):
+    """Whole-job throughput of independent replicas: all ranks' DoF*it per step
+    over the slowest rank's step time."""
+    return dof_per_rank * world / (ms_max * 1e-3)
+
+
 def flush_l2(torch, buf):
     buf.add_(1.0)
 
@@ -199,12 +218,8 @@ def run_ours(args):
     prof = plan.profile_read()
     plan.profile(False)
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    ms = float(np.mean(step_ms))
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = D * world / (ms * 1e-3)
+    ms = max_over_ranks(float(np.mean(step_ms)), world)
+    value = job_value(D, ms, world)
 
     if args.no_extras:
         if rank == 0:

@@ -60,6 +60,7 @@ struct EventPair {
 struct ac_plan {
     ac_problem prob;
     int M, L, logL, F, N, P, grid;
+    int P_upd, grid_upd;   // tile of the update kernel
     double dT;
     ac_alpha_schedule sched;
     int precision, inner, device;
@@ -330,7 +331,7 @@ static int stage_b(ac_plan* p, double* out, int accumulate, cudaStream_t st) {
     ua.L = p->L;
     ua.logL = p->logL;
     ua.F = p->F;
-    ua.P = p->P;
+    ua.P = p->P_upd;
     ua.X = p->X;
     ua.Pm = p->d_P;
     ua.tw = p->tw_L;
@@ -340,7 +341,7 @@ static int stage_b(ac_plan* p, double* out, int accumulate, cudaStream_t st) {
     ua.part = p->d_part_upd;
     {
         ProfScope ps(p, KK_UPD, st);
-        CK(ac::launch_upd<R>(ua, p->grid, smem, st));
+        CK(ac::launch_upd<R>(ua, p->grid_upd, smem, st));
         p->launches++;
     }
     return AC_OK;
@@ -526,10 +527,10 @@ static int richardson_loop(ac_plan* p, const double* u0, const double* b, int b_
         if (rc) return rc;
         if (sc.mode == AC_ALPHA_PAPER) m = m_next;
         if (sc.stop_rule == AC_STOP_PAPER) {
-            CK(cudaMemcpyAsync(p->h_part_upd, p->d_part_upd, sizeof(float) * p->grid, cudaMemcpyDeviceToHost, st));
+            CK(cudaMemcpyAsync(p->h_part_upd, p->d_part_upd, sizeof(float) * p->grid_upd, cudaMemcpyDeviceToHost, st));
             CK(cudaStreamSynchronize(st));
             float mx = 0.f;
-            for (int i = 0; i < p->grid; ++i) mx = std::max(mx, p->h_part_upd[i]);
+            for (int i = 0; i < p->grid_upd; ++i) mx = std::max(mx, p->h_part_upd[i]);
             S->diff_last[k] = mx;
         }
     }
@@ -689,6 +690,9 @@ int ac_setup(const ac_problem* prob, int M, int L, double dT, const ac_alpha_sch
     }
     p->P = P;
     p->grid = (p->N + P - 1) / P;
+    const int Pu = P;
+    p->P_upd = Pu;
+    p->grid_upd = (p->N + Pu - 1) / Pu;
 
     // device buffers
     cudaError_t e = cudaSuccess;
@@ -713,7 +717,7 @@ int ac_setup(const ac_problem* prob, int M, int L, double dT, const ac_alpha_sch
     AL(p->d_P, (size_t)F * M * M * cs);
     AL(p->d_mu, (size_t)F * M * cs);
     AL(p->d_part_fwd, sizeof(float) * p->grid);
-    AL(p->d_part_upd, sizeof(float) * p->grid);
+    AL(p->d_part_upd, sizeof(float) * p->grid_upd);
     p->part_d_len = std::max(2 * 152 * 2, 3 * 152 * 4);
     AL(p->d_part_d, sizeof(double) * p->part_d_len);
     AL(p->d_dtQ, sizeof(double) * M * M);
@@ -724,7 +728,7 @@ int ac_setup(const ac_problem* prob, int M, int L, double dT, const ac_alpha_sch
     }
 #undef AL
     if (e == cudaSuccess) e = cudaMallocHost((void**)&p->h_part_fwd, sizeof(float) * p->grid);
-    if (e == cudaSuccess) e = cudaMallocHost((void**)&p->h_part_upd, sizeof(float) * p->grid);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&p->h_part_upd, sizeof(float) * p->grid_upd);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&p->h_part_d, sizeof(double) * p->part_d_len);
     if (e == cudaSuccess && p->spatial_path == 3) e = cudaMallocHost((void**)&p->h_iters, sizeof(int) * F * M);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_res, cudaEventDisableTiming);  // spin: low latency
@@ -784,7 +788,7 @@ int ac_plan_get_info(const ac_plan* p, ac_plan_info* info) {
     info->L = p->L;
     info->F = p->F;
     info->tile_fwd = p->P;
-    info->tile_upd = p->P;
+    info->tile_upd = p->P_upd;
     info->spatial_path = p->spatial_path;
     info->workspace_bytes = p->workspace;
     info->launches = p->launches;

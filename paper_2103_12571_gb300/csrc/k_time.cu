@@ -20,6 +20,8 @@
 
 namespace ac {
 
+
+
 // Register copies of the stencil taps and a zero: on this GPU an FP64 FMA
 // whose operands all come from registers issues at the full FP64 rate, while
 // DMUL, DADD and FMAs with a constant-bank or immediate operand run about 16%
@@ -266,7 +268,7 @@ __global__ void __launch_bounds__(256) k_upd(UpdArgs a) {
     fft_inv<C, MM, true>(Z, a.logL, logHP, MM * HP, 1, HP, reinterpret_cast<const C*>(a.tw));
 
     float emax = 0.f;
-    const bool pairs = (N & 1) == 0;
+    const bool pairs = (N & 1) == 0 && a.out_aligned16;
 #pragma unroll 4
     for (int idx = threadIdx.x; idx < L * MM * HP; idx += blockDim.x) {
         const int q = idx & (HP - 1);
@@ -327,8 +329,16 @@ cudaError_t launch_fwd(const FwdArgs& a, int grid, size_t smem, cudaStream_t st)
     return cudaErrorInvalidValue;
 }
 
+static bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
+
+size_t upd_smem(const UpdArgs& a, size_t rsize) { return (size_t)a.L * a.M * a.P * rsize; }
+
 template <typename R>
-cudaError_t launch_upd(const UpdArgs& a, int grid, size_t smem, cudaStream_t st) {
+cudaError_t launch_upd(const UpdArgs& a_in, int grid, size_t smem_unused, cudaStream_t st) {
+    (void)smem_unused;
+    UpdArgs a = a_in;
+    a.out_aligned16 = aligned16(a.out);   // double2 accesses only on 16-byte aligned buffers
+    const size_t smem = upd_smem(a, sizeof(R));
     switch (a.M) {
 #define AC_CASE(MMV)                                                                          \
     case MMV: {                                                                               \

@@ -42,6 +42,7 @@ struct UpdArgs {
     const double* sinv;          // [L] alpha^{-l/L} / L
     double* out;                 // L*M*N
     int accumulate;              // 1: out += e, 0: out = e
+    int out_aligned16;           // out is 16-byte aligned (set by launch_upd): vector and async access allowed
     float* part;                 // [gridDim.x] max |e| over the last time block
 };
 
@@ -87,6 +88,8 @@ struct GradArgs {
 
 template <typename R> cudaError_t launch_fwd(const FwdArgs& a, int grid, size_t smem, cudaStream_t st);
 template <typename R> cudaError_t launch_upd(const UpdArgs& a, int grid, size_t smem, cudaStream_t st);
+// shared memory the update kernel needs for these arguments (rsize = bytes per real of the transform)
+size_t upd_smem(const UpdArgs& a, size_t rsize);
 template <typename R> cudaError_t launch_space_1d(const SpaceArgs& a, cudaStream_t st);
 template <typename R> cudaError_t launch_space_2d_small(const SpaceArgs& a, cudaStream_t st);
 template <typename R> cudaError_t launch_space_rows(const SpaceArgs& a, int inverse, cudaStream_t st);

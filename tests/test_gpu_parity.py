@@ -215,3 +215,26 @@ def test_richardson_solve_bicgstab(prob, precision, alpha_mode, tol, tau):
     assert all(v > 0 for v in st["inner_iters"]), st
     if precision == "c128":   # in complex64, systems stagnating at the FP32 floor are expected
         assert not any(st["inner_failed"]), st
+
+
+def test_unaligned_buffers_take_the_scalar_path():
+    """A caller may pass buffers that are only 8-byte aligned (a view one
+    double into a tensor); vector and asynchronous accesses are then off and
+    the results must not change."""
+    torch = torch_cuda()
+    from paper_2103_12571_gb300.api import Plan
+    prob = workloads.problem(2, 32, 16, nu=0.05, cx=0.3, order=2, M=3, L=8, T=0.1)
+    N = 32 * 16
+    rng = np.random.default_rng(12)
+    u0 = to_dev(torch, rng.standard_normal(N))
+    base = to_dev(torch, rng.standard_normal(8 * 3 * N))
+    plan = Plan(prob, precision="c64")
+    ua = base.clone().reshape(8, 3, N)
+    big = torch.empty(8 * 3 * N + 1, dtype=torch.float64, device="cuda")
+    ub = big[1:].view(8, 3, N)          # 8-byte aligned only
+    ub.copy_(ua)
+    for _ in range(2):
+        plan.richardson_step(3e-3, u0, ua)
+        plan.richardson_step(3e-3, u0, ub)
+    torch.cuda.synchronize()
+    assert torch.equal(ua, ub)
