@@ -55,6 +55,11 @@ extern "C" {
 #define AC_STOP_RESIDUAL 0  /* ||w - C u||_2 <= tol ||w||_2                               */
 #define AC_STOP_PAPER    1  /* Algorithm 2: m_k <= tol, or ||u_L^{k+1} - u_L^k||_inf <= tol */
 
+#define AC_FORM_CORRECTION 0  /* u^{k+1} = u^k + C_alpha^{-1}(w - C u^k): FP64 residual, iterative refinement */
+#define AC_FORM_PAPER      1  /* eq. (Riteration) as written: C_alpha u^{k+1} = w + (C_alpha - C) u^k,
+                                 whose right-hand side differs from w only by -alpha H u_L^k in block 1;
+                                 requires AC_STOP_PAPER                                                   */
+
 #define AC_MAX_STATS 128
 
 /* Spatial operator A = nu * Lap_h - cx * D_x - cy * D_y on the periodic box
@@ -80,13 +85,15 @@ typedef struct {
     int max_iter;     /* outer iteration cap (<= AC_MAX_STATS)                        */
     int stop_rule;    /* AC_STOP_RESIDUAL | AC_STOP_PAPER                             */
     int inner_max_iter; /* BiCGStab iteration cap per system (<= 0: 4000)             */
+    int form;           /* AC_FORM_CORRECTION | AC_FORM_PAPER                           */
 } ac_alpha_schedule;
 
 /* Per-solve record (host memory, filled by the solve calls). */
 typedef struct {
     int iters;                        /* outer iterations performed                    */
     int converged;                    /* 1 if the stop rule was met                     */
-    double res_rel[AC_MAX_STATS];     /* ||w - C u^(k)||_2 / ||w||_2, k = 0..iters      */
+    double res_rel[AC_MAX_STATS];     /* ||w - C u^(k)||_2 / ||w||_2, k = 0..iters
+                                         (AC_FORM_PAPER: only k = iters, the returned iterate) */
     double alpha[AC_MAX_STATS];       /* alpha_{k+1} used in iteration k                */
     double m[AC_MAX_STATS];           /* Algorithm 2's m_k (0 for other modes)          */
     double diff_last[AC_MAX_STATS];   /* ||u_L^{(k+1)} - u_L^{(k)}||_inf                 */

@@ -22,6 +22,7 @@ AC_C128, AC_C64 = 0, 1
 AC_INNER_FFT, AC_INNER_BICGSTAB = 0, 1
 AC_ALPHA_FIXED, AC_ALPHA_PAPER, AC_ALPHA_MIXED = 0, 1, 2
 AC_STOP_RESIDUAL, AC_STOP_PAPER = 0, 1
+AC_FORM_CORRECTION, AC_FORM_PAPER = 0, 1
 AC_MAX_STATS = 128
 
 
@@ -34,7 +35,7 @@ class Problem(ctypes.Structure):
 class Schedule(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int), ("alpha0", ctypes.c_double), ("m0", ctypes.c_double),
                 ("tau", ctypes.c_double), ("max_iter", ctypes.c_int), ("stop_rule", ctypes.c_int),
-                ("inner_max_iter", ctypes.c_int)]
+                ("inner_max_iter", ctypes.c_int), ("form", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):

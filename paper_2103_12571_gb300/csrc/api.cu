@@ -243,8 +243,8 @@ static double inner_tau(const ac_plan* p) {
 // out (+)= C_alpha^{-1} (w - C u)   [u may be null: out (+)= C_alpha^{-1} w]
 template <typename R>
 static int stage_a(ac_plan* p, const double* u, const double* u0, const double* b, int b_rev, int transposed,
-                   cudaStream_t st, bool record_res) {
-    ac::FwdArgs fa;
+                   cudaStream_t st, bool record_res, int recompute = 0, bool fwd_only = false) {
+    ac::FwdArgs fa{};
     fa.g = transposed ? p->grid_adj : p->grid_fwd;
     fa.M = p->M;
     fa.L = p->L;
@@ -256,6 +256,8 @@ static int stage_a(ac_plan* p, const double* u, const double* u0, const double* 
     fa.b = b;
     fa.b_reversed = b_rev;
     fa.transposed = transposed;
+    fa.recompute = recompute;
+    fa.alpha = p->cur_alpha;
     fa.qs = p->d_qs;
     fa.s = p->d_s;
     fa.inv_s_w = p->d_inv_s_w;
@@ -273,7 +275,8 @@ static int stage_a(ac_plan* p, const double* u, const double* u0, const double* 
         CK(cudaMemcpyAsync(p->h_part_fwd, p->d_part_fwd, sizeof(float) * p->grid, cudaMemcpyDeviceToHost, st));
         CK(cudaEventRecord(p->ev_res, st));
     }
-    ac::SpaceArgs sa;
+    if (fwd_only) return AC_OK;
+    ac::SpaceArgs sa{};
     sa.nx = p->prob.nx;
     sa.ny = p->prob.dim == 2 ? p->prob.ny : 1;
     sa.lognx = ilog2(sa.nx);
@@ -302,7 +305,7 @@ static int stage_a(ac_plan* p, const double* u, const double* u0, const double* 
             CK(ac::launch_space_rows<R>(sa, 1, st));
             p->launches += 3;
         } else if (p->spatial_path == 3) {
-            ac::BicgArgs ba;
+            ac::BicgArgs ba{};
             ba.g = transposed ? p->grid_adj : p->grid_fwd;
             ba.planes = p->F * p->M;
             ba.M = p->M;
@@ -323,9 +326,9 @@ static int stage_a(ac_plan* p, const double* u, const double* u0, const double* 
 }
 
 template <typename R>
-static int stage_b(ac_plan* p, double* out, int accumulate, cudaStream_t st) {
+static int stage_b(ac_plan* p, double* out, int accumulate, cudaStream_t st, int diff_last = 0) {
     const size_t smem = (size_t)p->L * p->M * p->P * sizeof(R);
-    ac::UpdArgs ua;
+    ac::UpdArgs ua{};
     ua.N = p->N;
     ua.M = p->M;
     ua.L = p->L;
@@ -338,6 +341,7 @@ static int stage_b(ac_plan* p, double* out, int accumulate, cudaStream_t st) {
     ua.sinv = p->d_sinv;
     ua.out = out;
     ua.accumulate = accumulate;
+    ua.diff_last = diff_last;
     ua.part = p->d_part_upd;
     {
         ProfScope ps(p, KK_UPD, st);
@@ -348,14 +352,27 @@ static int stage_b(ac_plan* p, double* out, int accumulate, cudaStream_t st) {
 }
 
 static int precond_a(ac_plan* p, const double* u, const double* u0, const double* b, int b_rev, int transposed,
-                     cudaStream_t st, bool record_res) {
-    if (p->precision == AC_C128) return stage_a<double>(p, u, u0, b, b_rev, transposed, st, record_res);
-    return stage_a<float>(p, u, u0, b, b_rev, transposed, st, record_res);
+                     cudaStream_t st, bool record_res, int recompute = 0, bool fwd_only = false) {
+    if (p->precision == AC_C128)
+        return stage_a<double>(p, u, u0, b, b_rev, transposed, st, record_res, recompute, fwd_only);
+    return stage_a<float>(p, u, u0, b, b_rev, transposed, st, record_res, recompute, fwd_only);
 }
 
-static int precond_b(ac_plan* p, double* out, int accumulate, cudaStream_t st) {
-    if (p->precision == AC_C128) return stage_b<double>(p, out, accumulate, st);
-    return stage_b<float>(p, out, accumulate, st);
+static int precond_b(ac_plan* p, double* out, int accumulate, cudaStream_t st, int diff_last = 0) {
+    if (p->precision == AC_C128) return stage_b<double>(p, out, accumulate, st, diff_last);
+    return stage_b<float>(p, out, accumulate, st, diff_last);
+}
+
+// ||w - C u||_2 with the residual kernel alone (its transform output is unused)
+static int residual_only(ac_plan* p, const double* u, const double* u0, const double* b, int b_rev, int transposed,
+                         double wscale, double wn2, double* res, cudaStream_t st) {
+    int rc = precond_a(p, u, u0, b, b_rev, transposed, st, true, 0, true);
+    if (rc) return rc;
+    CK(cudaEventSynchronize(p->ev_res));
+    double s = 0.0;
+    for (int i = 0; i < p->grid; ++i) s += p->h_part_fwd[i];
+    *res = std::sqrt(s) * wscale / wn2;
+    return AC_OK;
 }
 
 static int precond(ac_plan* p, const double* u, const double* u0, const double* b, int b_rev, int transposed,
@@ -476,6 +493,50 @@ static int richardson_loop(ac_plan* p, const double* u0, const double* b, int b_
     // alpha + L (3 eps + tau) / alpha, minimal at this alpha; Algorithm 2's
     // alpha_k (which tend to 1/2) are capped there
     const double alpha_mixed = std::min(0.25, std::max(1e-8, std::sqrt(p->L * (3.0 * eps + tau))));
+    if (sc.form == AC_FORM_PAPER) {
+        // eq. (Riteration) as printed, with Algorithm 2's loop and stop test
+        if (sc.stop_rule != AC_STOP_PAPER)
+            return fail(AC_ERR_INVALID_ARG, "AC_FORM_PAPER needs AC_STOP_PAPER (the form has no residual)");
+        for (int k = 0; k < max_iter; ++k) {
+            if (sc.mode == AC_ALPHA_PAPER && m <= tol) {
+                S->converged = 1;
+                break;
+            }
+            double alpha = sc.mode == AC_ALPHA_FIXED ? sc.alpha0 : alpha_mixed;
+            double m_next = 0.0;
+            if (sc.mode == AC_ALPHA_PAPER) {
+                alpha = std::min(0.5, std::max(std::sqrt(gam / m), 1e-12));   // alpha_{k+1} = sqrt(gamma / m_k)
+                m_next = 2.0 * std::sqrt(m * gam);                             // m_{k+1} = 2 sqrt(m_k gamma)
+            }
+            rc = ensure_tables(p, alpha, transposed, wscale, st);
+            if (rc) return rc;
+            rc = precond_a(p, u, u0, b, b_rev, transposed, st, false, 1);
+            if (rc) return rc;
+            rc = precond_b(p, u, 0, st, 1);
+            if (rc) return rc;
+            CK(cudaMemcpyAsync(p->h_part_upd, p->d_part_upd, sizeof(float) * p->grid_upd, cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            float mx = 0.f;
+            for (int i = 0; i < p->grid_upd; ++i) mx = std::max(mx, p->h_part_upd[i]);
+            S->alpha[k] = alpha;
+            S->m[k] = sc.mode == AC_ALPHA_PAPER ? m : 0.0;
+            S->diff_last[k] = mx;
+            S->iters = k + 1;
+            if (sc.mode == AC_ALPHA_PAPER) m = m_next;
+            if (!std::isfinite(mx)) return fail(AC_ERR_NOT_FINITE, "iterate not finite at iteration %d", k);
+            if (mx <= tol) {
+                S->converged = 1;
+                break;
+            }
+        }
+        double res = 0.0;
+        rc = residual_only(p, u, u0, b, b_rev, transposed, wscale, wn2, &res, st);
+        if (rc) return rc;
+        S->res_rel[S->iters] = res;
+        CK(cudaStreamSynchronize(st));
+        return S->converged ? AC_OK
+                            : fail(AC_ERR_NO_CONVERGENCE, "Algorithm 2 not converged after %d iterations", S->iters);
+    }
     int grew = 0;
     double prev_res = 1e300;
     for (int k = 0;; ++k) {
@@ -798,7 +859,7 @@ int ac_plan_get_info(const ac_plan* p, ac_plan_info* info) {
 static int apply_impl(ac_plan* p, const double* u, double* out, int transposed, void* stream) {
     if (!p || !u || !out) return fail(AC_ERR_INVALID_ARG, "null argument");
     cudaStream_t st = (cudaStream_t)stream;
-    ac::ApplyArgs a;
+    ac::ApplyArgs a{};
     a.g = transposed ? p->grid_adj : p->grid_fwd;
     a.M = p->M;
     a.L = p->L;
@@ -879,7 +940,7 @@ int ac_adjoint_solve(ac_plan* p, const double* g, double* lam, double tol, ac_st
 int ac_grad_params(ac_plan* p, const double* u, const double* lam, double* du0, double* dparams, void* stream) {
     if (!p || !u || !lam || !dparams) return fail(AC_ERR_INVALID_ARG, "null argument");
     cudaStream_t st = (cudaStream_t)stream;
-    ac::GradArgs a;
+    ac::GradArgs a{};
     a.g = p->grid_fwd;
     a.M = p->M;
     a.L = p->L;

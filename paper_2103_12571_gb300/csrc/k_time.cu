@@ -39,6 +39,32 @@ __device__ __forceinline__ void residual_point(const FwdArgs& a, const RegCoef& 
     const long N = g.N;
     const double s = a.s[l];
     const int lb = a.b_reversed ? (a.L - 1 - l) : l;
+    if (a.recompute) {
+        // right-hand side of eq. (Riteration): w + (C_alpha - C) u, where
+        // (C_alpha - C) u = -alpha (H u_L) in block 1 (H^T u_L for the adjoint)
+#pragma unroll
+        for (int m = 0; m < MM; ++m) {
+            double w = (l == 0 && a.u0) ? a.u0[n] : 0.0;
+            if (a.b) w += a.b[((long)lb * MM + m) * N + n];
+            r[m] = w;
+        }
+        if (l == 0) {
+            const double* uL = a.u + (long)(a.L - 1) * MM * N + n;
+            if (!a.transposed) {
+                const double c = -a.alpha * uL[(long)(MM - 1) * N];
+#pragma unroll
+                for (int m = 0; m < MM; ++m) r[m] += c;
+            } else {
+                double c = 0.0;
+#pragma unroll
+                for (int j = 0; j < MM; ++j) c += uL[(long)j * N];
+                r[MM - 1] += -a.alpha * c;
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < MM; ++m) r[m] = fma(s, r[m], k.zero);
+        return;
+    }
     if (!a.u) {
 #pragma unroll
         for (int m = 0; m < MM; ++m) {
@@ -279,10 +305,15 @@ __global__ void __launch_bounds__(256) k_upd(UpdArgs a) {
         const double sv = a.sinv[l];
         double* o = a.out + ((long)l * MM + m) * N + nn;
         const double za = to_double(z.x), zb = to_double(z.y);
-        if (l == L - 1) {
+        if (l == L - 1 && !a.diff_last) {
             const float zx = sizeof(R) == 4 ? (float)z.x : d2f_int((double)z.x);
             const float zy = sizeof(R) == 4 ? (float)z.y : d2f_int((double)z.y);
             emax = fmaxf(emax, fmaxf(fabsf(zx), fabsf(zy)) * d2f_int(sv));
+        }
+        double prev0 = 0.0, prev1 = 0.0;
+        if (a.diff_last && l == L - 1) {
+            if (nn < N) prev0 = o[0];
+            if (nn + 1 < N) prev1 = o[1];
         }
         if (nn + 1 < N && pairs) {
             double2 v = a.accumulate ? *reinterpret_cast<double2*>(o) : make_double2(0.0, 0.0);
@@ -292,6 +323,9 @@ __global__ void __launch_bounds__(256) k_upd(UpdArgs a) {
         } else {
             if (nn < N) o[0] = fma(sv, za, a.accumulate ? o[0] : 0.0);
             if (nn + 1 < N) o[1] = fma(sv, zb, a.accumulate ? o[1] : 0.0);
+        }
+        if (a.diff_last && l == L - 1) {   // overwrite mode: |u_L^{k+1} - u_L^k| (old values read above)
+            emax = fmaxf(emax, fmaxf(d2f_int(fabs(prev0 - sv * za)), d2f_int(fabs(prev1 - sv * zb))));
         }
     }
     const float tot = block_max(emax, red);

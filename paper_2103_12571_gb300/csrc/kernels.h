@@ -23,6 +23,8 @@ struct FwdArgs {
     const double* b;             // L*M*N or null: full right-hand side
     int b_reversed;              // read b[L-1-l] instead of b[l]
     int transposed;              // coupling H^T (adjoint) instead of H
+    int recompute;               // paper's form: r = w + (C_alpha - C) u, i.e. w - alpha H u_L in block 1 only
+    double alpha;                // alpha of the recompute form
     const double* qs;            // [L][M][M] s_l * dT * Q (Q^T if transposed)
     const double* s;             // [L] s_l = alpha^{l/L}
     const float* inv_s_w;        // [L] 1 / (s_l * w_scale) for the residual norm
@@ -42,7 +44,8 @@ struct UpdArgs {
     const double* sinv;          // [L] alpha^{-l/L} / L
     double* out;                 // L*M*N
     int accumulate;              // 1: out += e, 0: out = e
-    int out_aligned16;           // out is 16-byte aligned (set by launch_upd): vector and async access allowed
+    int out_aligned16;           // out is 16-byte aligned (set by launch_upd): double2 access allowed
+    int diff_last;               // with accumulate = 0: part = max |out_new - out_old| over the last time block
     float* part;                 // [gridDim.x] max |e| over the last time block
 };
 

@@ -209,7 +209,7 @@ int run(const ac_problem* prob, int M, int L, double dT, double alpha, const dou
     }
     g.c0 = tx[2] + ty[2];
 
-    ac::FwdArgs fa;
+    ac::FwdArgs fa{};
     fa.g = g;
     fa.M = M;
     fa.L = L;
@@ -231,7 +231,7 @@ int run(const ac_problem* prob, int M, int L, double dT, double alpha, const dou
     const size_t smem = (size_t)L * M * P * sizeof(R);
     chk(ac::launch_fwd<R>(fa, grid, smem, st));
 
-    ac::SpaceArgs sa;
+    ac::SpaceArgs sa{};
     sa.nx = nx;
     sa.ny = ny;
     sa.lognx = log2i(nx);
@@ -254,7 +254,7 @@ int run(const ac_problem* prob, int M, int L, double dT, double alpha, const dou
         chk(ac::launch_space_rows<R>(sa, 1, st));
     }
 
-    ac::UpdArgs ua;
+    ac::UpdArgs ua{};
     ua.N = (int)N;
     ua.M = M;
     ua.L = L;

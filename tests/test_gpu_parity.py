@@ -238,3 +238,65 @@ def test_unaligned_buffers_take_the_scalar_path():
         plan.richardson_step(3e-3, u0, ub)
     torch.cuda.synchronize()
     assert torch.equal(ua, ub)
+
+
+# ------------------------------------------------- eq. (Riteration) as printed
+@pytest.mark.parametrize("prob", [SMALL[0], SMALL[4], SMALL[6]], ids=ids)
+def test_paper_form_iterates_match_oracle(prob):
+    """AC_FORM_PAPER: u^{k+1} = C_alpha^{-1}(w - alpha H u_L^k e_1), compared
+    iterate by iterate with the oracle's recompute-form Richardson."""
+    torch = torch_cuda()
+    from paper_2103_12571_gb300.api import Plan
+    Q, A, dT = oracle_setup(prob)
+    rng = np.random.default_rng(13)
+    N = operators.n_points(prob)
+    u0 = rng.standard_normal(N)
+    alpha = 1e-3
+    its = paradiag.richardson(A, Q, dT, prob["L"], u0, [alpha] * 3, form="paper")
+    for k in (1, 2, 3):
+        plan = Plan(prob, precision="c128", alpha="fixed", alpha0=alpha, max_iter=k, stop="paper", form="paper")
+        u, st = plan.solve(to_dev(torch, u0), tol=0.0, raise_on_fail=False)
+        assert st["iters"] == k
+        err = rel2(u.cpu().numpy(), its[k])
+        assert err < 20 * prob["L"] * 3 * EPS64 / alpha, (k, err)
+        # the recorded last-step difference is the paper's stop quantity
+        assert abs(st["diff_last"][-1] - np.max(np.abs(its[k][-1] - its[k - 1][-1]))) < 1e-6 * max(st["diff_last"][-1], 1e-30) + 1e-13
+
+
+def test_paper_form_algorithm2_converges_and_follows_the_alpha_recursion():
+    torch = torch_cuda()
+    from oracle import alpha_rule
+    from paper_2103_12571_gb300.api import Plan
+    prob = SMALL[4]
+    Q, A, dT = oracle_setup(prob)
+    rng = np.random.default_rng(14)
+    N = operators.n_points(prob)
+    u0 = rng.standard_normal(N)
+    ref = sequential.sequential_solve(A, Q, dT, prob["L"], u0)
+    m0 = 0.5
+    plan = Plan(prob, precision="c128", alpha="paper", m0=m0, max_iter=20, stop="paper", form="paper")
+    u, st = plan.solve(to_dev(torch, u0), tol=1e-12, raise_on_fail=False)
+    assert st["converged"], st
+    assert rel2(u.cpu().numpy(), ref) < 1e-9
+    gam = alpha_rule.gamma(prob["L"], EPS64, 0.0, np.max(np.abs(u0)))
+    alphas, ms = alpha_rule.alpha_sequence(m0, gam, kmax=st["iters"])
+    np.testing.assert_allclose(st["alpha"], alphas, rtol=1e-12)
+    np.testing.assert_allclose(st["m"][:st["iters"]], ms[:st["iters"]], rtol=1e-12)
+    assert 0 < st["res_rel"][-1] < 1e-9
+
+
+def test_paper_form_in_complex64_stalls_where_the_correction_form_refines():
+    """Without a residual the complex64 preconditioner's round-off stays in
+    the answer (about L eps_32 / alpha); the correction form refines it away."""
+    torch = torch_cuda()
+    from paper_2103_12571_gb300.api import Plan
+    prob = SMALL[4]
+    Q, A, dT = oracle_setup(prob)
+    u0 = np.random.default_rng(15).standard_normal(operators.n_points(prob))
+    ref = sequential.sequential_solve(A, Q, dT, prob["L"], u0)
+    p1 = Plan(prob, precision="c64", alpha="fixed", alpha0=1e-2, max_iter=30, stop="paper", form="paper")
+    u1, _ = p1.solve(to_dev(torch, u0), tol=1e-14, raise_on_fail=False)
+    p2 = Plan(prob, precision="c64", alpha="mixed", max_iter=30)
+    u2, _ = p2.solve(to_dev(torch, u0), tol=1e-13, raise_on_fail=False)
+    e1, e2 = rel2(u1.cpu().numpy(), ref), rel2(u2.cpu().numpy(), ref)
+    assert e1 > 1e-8 and e2 < 1e-10, (e1, e2)
