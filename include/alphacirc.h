@@ -139,6 +139,13 @@ int ac_apply_C(ac_plan* plan, const double* u, double* Cu, void* stream);
 /* out = C^T lam (FP64).  lam, out: device, L*M*N doubles. */
 int ac_apply_CT(ac_plan* plan, const double* lam, double* out, void* stream);
 
+/* v_l = dT (Q (x) I_N) b_l for l = 0..L-1: the forcing part of the right-hand
+ * side of eq. (collocation) / (seq_collocation_problem), from samples
+ * bnodes[l][m][n] = b(T_l + dT t_m, x_n) of the forcing at the collocation
+ * nodes of step l.  Pass v as the `b` argument of the solve calls.
+ * bnodes, v: device, L*M*N doubles, distinct.  FP64. */
+int ac_collocation_rhs(ac_plan* plan, const double* bnodes, double* v, void* stream);
+
 /* ---- one preconditioner solve (Lemma 1, eqs. (s1)-(s3), Algorithm 1) ---- */
 
 /* e = C_alpha^{-1} r with C_alpha = I_L (x) C_coll + E_alpha (x) H (eq. (prec)):

@@ -157,3 +157,9 @@ def residual(u, u0, A, Q, dT, b=None):
     """r = w - C u."""
     L, M, N = u.shape
     return rhs_w(u0, L, M, b) - apply_C(u, A, Q, dT)
+
+
+def collocation_rhs(bnodes, Q, dT):
+    """v_l = dT (Q (x) I_N) b_l for forcing samples bnodes[l][m][n] at the
+    collocation nodes T_l + dT t_m of step l (eq. (collocation), Sec. 2.1)."""
+    return dT * np.einsum("mj,ljn->lmn", Q, bnodes)

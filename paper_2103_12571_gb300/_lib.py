@@ -64,6 +64,7 @@ _PROTOS = {
     "ac_apply_C": (_I, [_P, _P, _P, _P]),
     "ac_apply_CT": (_I, [_P, _P, _P, _P]),
     "ac_precond_solve": (_I, [_P, _D, _P, _P, _P]),
+    "ac_collocation_rhs": (_I, [_P, _P, _P, _P]),
     "ac_richardson_step": (_I, [_P, _D, _P, _P, _P, ctypes.POINTER(_D), _P]),
     "ac_richardson_solve": (_I, [_P, _P, _P, _P, _I, _D, ctypes.POINTER(Stats), _P]),
     "ac_adjoint_solve": (_I, [_P, _P, _P, _D, ctypes.POINTER(Stats), _P]),

@@ -96,6 +96,15 @@ class Plan:
         C.check(C.lib().ac_apply_CT(self._h, _ptr(lam), _ptr(out), _stream()), "ac_apply_CT")
         return out
 
+    def collocation_rhs(self, bnodes, out=None):
+        """v_l = dT (Q (x) I) b_l from forcing samples at the collocation nodes."""
+        out = self.empty() if out is None else out
+        C.check(C.lib().ac_collocation_rhs(self._h, _ptr(bnodes), _ptr(out), _stream()), "ac_collocation_rhs")
+        return out
+
+    def nodes(self):
+        return radau_nodes(self.M)
+
     def precond_solve(self, alpha, r, out=None):
         out = self.empty() if out is None else out
         C.check(C.lib().ac_precond_solve(self._h, float(alpha), _ptr(r), _ptr(out), _stream()),

@@ -21,6 +21,8 @@ cudaError_t launch_wnorms(const double* u0, const double* b, int L, int M, long 
                           int grid, cudaStream_t st);
 cudaError_t launch_fill_stack(const double* u0, double* u, int L, int M, long long N, cudaStream_t st);
 cudaError_t launch_a_inf(const Grid& g, const double* u0, double* part, int grid, cudaStream_t st);
+cudaError_t launch_colloc_rhs(const double* b, const double* dtQ, double* v, int L, int M, long long N,
+                              cudaStream_t st);
 }
 
 using ac::cd;
@@ -874,6 +876,15 @@ static int apply_impl(ac_plan* p, const double* u, double* out, int transposed, 
 }
 
 int ac_apply_C(ac_plan* p, const double* u, double* Cu, void* stream) { return apply_impl(p, u, Cu, 0, stream); }
+
+int ac_collocation_rhs(ac_plan* p, const double* bnodes, double* v, void* stream) {
+    if (!p || !bnodes || !v || bnodes == v) return fail(AC_ERR_INVALID_ARG, "bad argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    ProfScope ps(p, KK_AUX, st);
+    CK(ac::launch_colloc_rhs(bnodes, p->d_dtQ, v, p->L, p->M, p->N, st));
+    p->launches++;
+    return AC_OK;
+}
 int ac_apply_CT(ac_plan* p, const double* lam, double* out, void* stream) {
     return apply_impl(p, lam, out, 1, stream);
 }

@@ -271,6 +271,32 @@ cudaError_t launch_a_inf(const Grid& g, const double* u0, double* part, int grid
     return cudaGetLastError();
 }
 
+// v[l][m][n] = sum_j dtQ[m][j] b[l][j][n]
+__global__ void k_colloc_rhs(const double* b, const double* dtQ, double* v, int L, int M, long N) {
+    const long total = (long)L * N;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+        const int l = (int)(t / N);
+        const long n = t - (long)l * N;
+        const double* bl = b + (long)l * M * N + n;
+        double bj[8];
+        for (int j = 0; j < M; ++j) bj[j] = bl[(long)j * N];
+        for (int m = 0; m < M; ++m) {
+            double acc = 0.0;
+            for (int j = 0; j < M; ++j) acc = fma(dtQ[m * M + j], bj[j], acc);
+            v[((long)l * M + m) * N + n] = acc;
+        }
+    }
+}
+
+cudaError_t launch_colloc_rhs(const double* b, const double* dtQ, double* v, int L, int M, long long N,
+                              cudaStream_t st) {
+    const long total = (long)L * N;
+    int grid = (int)((total + 255) / 256);
+    if (grid > 152 * 16) grid = 152 * 16;
+    k_colloc_rhs<<<grid, 256, 0, st>>>(b, dtQ, v, L, M, N);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_fill_stack(const double* u0, double* u, int L, int M, long long N, cudaStream_t st) {
     const long total = (long)L * M * N;
     int grid = (int)((total + 255) / 256);

@@ -94,3 +94,30 @@ def config(i):
         p = problem(2, 512, 512, nu=1e-3, cx=1.0, cy=0.5, order=2, M=3, L=512, T=2.0)
         return p, random_phase_bumps_2d(512, 512, 8.0, seed=0), dict(name="advdiff2d_512x512_M3_L512")
     raise ValueError(i)
+
+
+# ---- the paper's forced heat test (Sec. 5, eq. (heat)) on [pi, pi + T] x [0,1]^2
+HEAT_T0 = np.pi
+
+
+def heat_forcing_problem(n, order=2, M=3, L=16, T=0.1):
+    """u_t = Lap u + sin(2 pi x) sin(2 pi y) (8 pi^2 cos t - sin t), periodic."""
+    return problem(2, n, n, nu=1.0, order=order, M=M, L=L, T=T)
+
+
+def heat_forcing_field(n):
+    """phi(x, y) = sin(2 pi x) sin(2 pi y) on the n x n grid (flat index iy*n + ix)."""
+    x = _grid(n)
+    return (np.sin(2 * np.pi * x)[None, :] * np.sin(2 * np.pi * x)[:, None]).reshape(-1)
+
+
+def heat_forcing_samples(n, times):
+    """b at the given times (array of shape (L, M)): b[l, m] = (8 pi^2 cos t - sin t) phi."""
+    times = np.asarray(times)
+    f = 8 * np.pi ** 2 * np.cos(times) - np.sin(times)
+    return f[..., None] * heat_forcing_field(n)[None, None, :]
+
+
+def heat_forcing_u0(n):
+    """u(pi) of the solution cos(t) phi (see the design doc on the printed forcing)."""
+    return np.cos(HEAT_T0) * heat_forcing_field(n)

@@ -397,3 +397,44 @@ def test_workloads_deterministic_and_shaped():
         np.testing.assert_array_equal(u0, u02)
     u = workloads.random_phase_bumps_2d(32, 32, 4.0, seed=1)
     assert abs(np.max(np.abs(u)) - 1) < 1e-15
+
+
+# ---------------------------------------------------- forcing (eq. (heat))
+def _forced_mode_exact(lam, t, t0, g0):
+    """g' = lam g + 8 pi^2 cos t - sin t, g(t0) = g0, in closed form."""
+    a, b = 8 * np.pi ** 2, -1.0
+    B = (a - lam * b) / (1 + lam ** 2)
+    A = -lam * B - b
+    gp = lambda s: A * np.cos(s) + B * np.sin(s)
+    return gp(t) + (g0 - gp(t0)) * np.exp(lam * (t - t0))
+
+
+def test_printed_heat_forcing_has_solution_cos_t():
+    # u = cos(t) phi satisfies u_t = Lap u + (8 pi^2 cos t - sin t) phi exactly
+    t = np.linspace(3.1, 3.5, 7)
+    assert np.allclose(_forced_mode_exact(-8 * np.pi ** 2, t, np.pi, np.cos(np.pi)), np.cos(t), atol=1e-13)
+
+
+@pytest.mark.parametrize("M", [1, 2, 3])
+def test_forced_collocation_converges_at_order_2M_minus_1(M):
+    """Forcing enters as v_l = dT (Q (x) I) b_l with b sampled at T_l + dT t_m
+    (eq. (collocation)); on one discrete Fourier mode the end-point error
+    against the semi-discrete exact solution falls like dT^(2M-1)."""
+    n = 16
+    phi = workloads.heat_forcing_field(n)
+    t = collocation.radau_iia_nodes(M)
+    Q = collocation.collocation_matrix(t)
+    errs = []
+    Ls = (4, 8, 16) if M < 3 else (2, 4, 8)
+    for L in Ls:
+        prob = workloads.heat_forcing_problem(n, order=2, M=M, L=L, T=0.1)
+        A = operators.spatial_operator(prob)
+        dT = prob["T"] / L
+        times = workloads.HEAT_T0 + dT * (np.arange(L)[:, None] + t[None, :])
+        v = operators.collocation_rhs(workloads.heat_forcing_samples(n, times), Q, dT)
+        u = sequential.sequential_solve(A, Q, dT, L, workloads.heat_forcing_u0(n), v)
+        lam = fourier.symbol(prob)[1, 1].real
+        g = _forced_mode_exact(lam, workloads.HEAT_T0 + prob["T"], workloads.HEAT_T0, -1.0)
+        errs.append(np.max(np.abs(u[-1, -1] - g * phi)))
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
+    assert abs(rates[-1] - (2 * M - 1)) < 0.4, (rates, errs)
