@@ -179,6 +179,18 @@ int ac_richardson_solve(ac_plan* plan, const double* u0, const double* b,
                         double* u, int init_u, double tol, ac_stats* stats,
                         void* stream);
 
+/* Moving window (Sec. 5.2, parallel scaling runs): n_windows consecutive
+ * all-at-once solves of L steps each; window w starts from the last node of
+ * window w-1 (u0 for w = 0).  u_end: device, N doubles, receives the state at
+ * the end of the last window.  work: device, L*M*N doubles (the window's
+ * iterate).  b is not supported here (unforced problems).  stats (host, may be
+ * NULL) receives the record of the last window; iters_total (host, may be
+ * NULL) the sum of the windows' iteration counts.  Returns the first failing
+ * window's status. */
+int ac_window_solve(ac_plan* plan, const double* u0, int n_windows, double* u_end,
+                    double* work, double tol, ac_stats* stats, int* iters_total,
+                    void* stream);
+
 /* ---- adjoint (not in the paper; derived from eq. (globalsys)) ----------- */
 
 /* lam = C^{-T} g.  Reversing the time index turns C^T into a system of the

@@ -68,6 +68,7 @@ _PROTOS = {
     "ac_richardson_step": (_I, [_P, _D, _P, _P, _P, ctypes.POINTER(_D), _P]),
     "ac_richardson_solve": (_I, [_P, _P, _P, _P, _I, _D, ctypes.POINTER(Stats), _P]),
     "ac_adjoint_solve": (_I, [_P, _P, _P, _D, ctypes.POINTER(Stats), _P]),
+    "ac_window_solve": (_I, [_P, _P, _I, _P, _P, _D, ctypes.POINTER(Stats), ctypes.POINTER(_I), _P]),
     "ac_grad_params": (_I, [_P, _P, _P, _P, _P, _P]),
     "ac_precond_solve_noalloc": (_I, [ctypes.POINTER(Problem), _I, _I, _D, _D, _I, _P, _P, _P]),
     "ac_radau_nodes": (_I, [_I, _P]),

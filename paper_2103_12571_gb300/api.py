@@ -129,6 +129,17 @@ class Plan:
             C.check(rc, "ac_richardson_solve")
         return u, stats_dict(st)
 
+    def window_solve(self, u0, n_windows, tol):
+        """Moving window: n_windows consecutive L-step solves; returns (u at
+        the end, total iterations, stats of the last window)."""
+        u_end = torch.empty(self.N, dtype=torch.float64, device="cuda")
+        work = self.empty()
+        st = C.Stats()
+        tot = ctypes.c_int(0)
+        C.check(C.lib().ac_window_solve(self._h, _ptr(u0), int(n_windows), _ptr(u_end), _ptr(work), float(tol),
+                                        ctypes.byref(st), ctypes.byref(tot), _stream()), "ac_window_solve")
+        return u_end, tot.value, stats_dict(st)
+
     def adjoint_solve(self, g, tol, lam=None, raise_on_fail=True):
         lam = self.empty() if lam is None else lam
         st = C.Stats()

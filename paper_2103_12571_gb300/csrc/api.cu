@@ -932,6 +932,29 @@ int ac_richardson_solve(ac_plan* p, const double* u0, const double* b, double* u
     return richardson_loop(p, u0, b, 0, 0, u, tol, stats, st);
 }
 
+int ac_window_solve(ac_plan* p, const double* u0, int n_windows, double* u_end, double* work, double tol,
+                    ac_stats* stats, int* iters_total, void* stream) {
+    if (!p || !u0 || !u_end || !work || n_windows < 1 || u_end == u0) return fail(AC_ERR_INVALID_ARG, "bad argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t blk = (size_t)p->N * sizeof(double);
+    const double* start = u0;
+    int total = 0;
+    for (int w = 0; w < n_windows; ++w) {
+        int rc = ac_richardson_solve(p, start, nullptr, work, 0, tol, stats, stream);
+        if (stats) total += stats->iters;
+        if (rc) {
+            if (iters_total) *iters_total = total;
+            return rc;
+        }
+        // last node of the last step: u[L-1][M-1][:]
+        CK(cudaMemcpyAsync(u_end, work + ((size_t)(p->L - 1) * p->M + (p->M - 1)) * p->N, blk,
+                           cudaMemcpyDeviceToDevice, st));
+        start = u_end;
+    }
+    if (iters_total) *iters_total = total;
+    return AC_OK;
+}
+
 int ac_adjoint_solve(ac_plan* p, const double* g, double* lam, double tol, ac_stats* stats, void* stream) {
     if (!p || !g || !lam || g == lam) return fail(AC_ERR_INVALID_ARG, "bad argument");
     cudaStream_t st = (cudaStream_t)stream;

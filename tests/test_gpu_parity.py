@@ -300,3 +300,18 @@ def test_paper_form_in_complex64_stalls_where_the_correction_form_refines():
     u2, _ = p2.solve(to_dev(torch, u0), tol=1e-13, raise_on_fail=False)
     e1, e2 = rel2(u1.cpu().numpy(), ref), rel2(u2.cpu().numpy(), ref)
     assert e1 > 1e-8 and e2 < 1e-10, (e1, e2)
+
+
+def test_moving_window_equals_long_sequential_sweep():
+    """Four windows of L = 8 steps cover the same 32 steps as one sequential
+    sweep of the oracle (Sec. 5.2's moving window)."""
+    torch = torch_cuda()
+    from paper_2103_12571_gb300.api import Plan
+    prob = workloads.problem(2, 32, 32, nu=0.02, cx=0.5, cy=0.25, order=2, M=3, L=8, T=0.05)
+    Q, A, dT = oracle_setup(prob)
+    u0 = workloads.random_phase_bumps_2d(32, 32, 4.0, seed=5)
+    ref = sequential.sequential_solve(A, Q, dT, 4 * prob["L"], u0)[-1, -1]
+    plan = Plan(prob, precision="c64", alpha="mixed", max_iter=30)
+    u_end, iters, st = plan.window_solve(to_dev(torch, u0), 4, tol=1e-13)
+    assert rel2(u_end.cpu().numpy(), ref) < 1e-10
+    assert iters >= 4 and st["converged"]
