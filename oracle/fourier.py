@@ -12,34 +12,40 @@ of the collocation method),
 """
 import numpy as np
 
-
-def symbol_d1(n, length=1.0, order=2):
-    """Eigenvalues of the periodic central first derivative, mode k = 0..n-1."""
-    h = length / n
-    th = 2 * np.pi * np.arange(n) / n
-    if order == 2:
-        return 1j * np.sin(th) / h
-    return 1j * (8 * np.sin(th) - np.sin(2 * th)) / (6 * h)
+from . import stencils
 
 
-def symbol_d2(n, length=1.0, order=2):
-    """Eigenvalues of the periodic central second derivative."""
-    h = length / n
-    th = 2 * np.pi * np.arange(n) / n
-    if order == 2:
-        return (2 * np.cos(th) - 2) / h ** 2
-    return (-2 * np.cos(2 * th) + 32 * np.cos(th) - 30) / (12 * h ** 2)
+def taps_symbol(n, taps, scale):
+    """Eigenvalues scale * sum_o w_o exp(2 pi i k o / n), k = 0..n-1, of the
+    periodic stencil {o: w_o} (e_k(x_j) = exp(2 pi i k j / n))."""
+    k = np.arange(n)
+    s = np.zeros(n, dtype=np.complex128)
+    for o, w in taps.items():
+        s += float(w) * np.exp(2j * np.pi * ((k * o) % n) / n)
+    return scale * s
+
+
+def symbol_d1(n, length=1.0, order=2, upwind=False, c=1.0):
+    """Eigenvalues of the periodic first derivative, mode k = 0..n-1."""
+    return taps_symbol(n, stencils.d1_weights(order, upwind, c), n / length)
+
+
+def symbol_d2(n, length=1.0, order=2, upwind=False):
+    """Eigenvalues of the periodic second derivative."""
+    return taps_symbol(n, stencils.d2_weights(order, upwind), (n / length) ** 2)
 
 
 def symbol(prob):
     """sigma(k) for A = nu Lap - c . grad; shape (nx,) in 1D, (ny, nx) in 2D
     (matching numpy.fft.fft2 of a field stored as [iy, ix])."""
     nx, lx, order = prob["nx"], prob.get("lx", 1.0), prob["order"]
-    sx = prob["nu"] * symbol_d2(nx, lx, order) - prob.get("cx", 0.0) * symbol_d1(nx, lx, order)
+    up = bool(prob.get("upwind", False))
+    cx, cy = prob.get("cx", 0.0), prob.get("cy", 0.0)
+    sx = prob["nu"] * symbol_d2(nx, lx, order, up) - cx * symbol_d1(nx, lx, order, up, cx)
     if prob["dim"] == 1:
         return sx
     ny, ly = prob["ny"], prob.get("ly", 1.0)
-    sy = prob["nu"] * symbol_d2(ny, ly, order) - prob.get("cy", 0.0) * symbol_d1(ny, ly, order)
+    sy = prob["nu"] * symbol_d2(ny, ly, order, up) - cy * symbol_d1(ny, ly, order, up, cy)
     return sy[:, None] + sx[None, :]
 
 

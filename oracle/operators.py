@@ -2,14 +2,12 @@
 infrastructure only).
 
 Problem (paper Sec. 2, eq. (genericlinearform)) with b = 0:  u_t = A u.
-A = nu * Laplacian_h - c . grad_h on a periodic grid, central differences of
-order 2 or 4 (the paper does not print the stencils; these are the standard
-central formulas):
-  first derivative,  order 2: (u_{j+1} - u_{j-1}) / (2h)
-                     order 4: (-u_{j+2} + 8u_{j+1} - 8u_{j-1} + u_{j-2}) / (12h)
-  second derivative, order 2: (u_{j+1} - 2u_j + u_{j-1}) / h^2
-                     order 4: (-u_{j+2} + 16u_{j+1} - 30u_j + 16u_{j-1} - u_{j-2}) / (12h^2)
-with h = length / n per axis and, in 2D, the flat index n = iy * nx + ix.
+A = nu * Laplacian_h - c . grad_h on a periodic grid.  The stencils are the
+finite-difference formulas of `stencils.py`: centred of order 2, 4 or 6, or,
+with prob["upwind"], an upwind first derivative of order 1..5 (biased
+against the sign of each velocity component) with the centred Laplacian of
+the order rounded up to even.  h = length / n per axis and, in 2D, the flat
+index n = iy * nx + ix.
 
 C_coll = I_{MN} - dT Q (x) A and H = H_M (x) I_N (Sec. 2.1);
 C = I_L (x) C_coll + E (x) H (eq. (globalsys)), E = -1 on the sub-diagonal;
@@ -19,13 +17,8 @@ in the top-right corner.
 import numpy as np
 import scipy.sparse as sp
 
+from . import stencils
 from .collocation import H_matrix
-
-_D1 = {2: {1: 0.5, -1: -0.5},
-       4: {2: -1.0 / 12, 1: 8.0 / 12, -1: -8.0 / 12, -2: 1.0 / 12}}
-_D2 = {2: {1: 1.0, 0: -2.0, -1: 1.0},
-       4: {2: -1.0 / 12, 1: 16.0 / 12, 0: -30.0 / 12, -1: 16.0 / 12, -2: -1.0 / 12}}
-
 
 def _periodic(n, taps, scale):
     """Sparse n x n periodic matrix with (Au)_j = scale * sum_o taps[o] u_{j+o}."""
@@ -43,30 +36,36 @@ def _periodic(n, taps, scale):
     return sp.csr_matrix((vals, (rows, cols)), shape=(n, n))
 
 
-def first_derivative_1d(n, length=1.0, order=2):
+def first_derivative_1d(n, length=1.0, order=2, upwind=False, c=1.0):
     h = length / n
-    return _periodic(n, _D1[order], 1.0 / h)
+    taps = {o: float(w) for o, w in stencils.d1_weights(order, upwind, c).items()}
+    return _periodic(n, taps, 1.0 / h)
 
 
-def second_derivative_1d(n, length=1.0, order=2):
+def second_derivative_1d(n, length=1.0, order=2, upwind=False):
     h = length / n
-    return _periodic(n, _D2[order], 1.0 / (h * h))
+    taps = {o: float(w) for o, w in stencils.d2_weights(order, upwind).items()}
+    return _periodic(n, taps, 1.0 / (h * h))
 
 
 def operator_parts(prob):
     """(Lap, Dx, Dy) sparse matrices for a problem dict
-    {dim, nx, ny, lx, ly, nu, cx, cy, order}.  Dy is None in 1D."""
+    {dim, nx, ny, lx, ly, nu, cx, cy, order[, upwind]}.  Dy is None in 1D.
+    With upwind stencils Dx and Dy depend on the signs of cx and cy."""
     dim, order = prob["dim"], prob["order"]
+    up = bool(prob.get("upwind", False))
+    stencils.check_scheme(order, up)
     nx, lx = prob["nx"], prob.get("lx", 1.0)
+    cx, cy = prob.get("cx", 0.0), prob.get("cy", 0.0)
     if dim == 1:
-        return (second_derivative_1d(nx, lx, order),
-                first_derivative_1d(nx, lx, order), None)
+        return (second_derivative_1d(nx, lx, order, up),
+                first_derivative_1d(nx, lx, order, up, cx), None)
     ny, ly = prob["ny"], prob.get("ly", 1.0)
     Ix, Iy = sp.identity(nx, format="csr"), sp.identity(ny, format="csr")
-    Lap = sp.kron(Iy, second_derivative_1d(nx, lx, order)) + \
-        sp.kron(second_derivative_1d(ny, ly, order), Ix)
-    Dx = sp.kron(Iy, first_derivative_1d(nx, lx, order))
-    Dy = sp.kron(first_derivative_1d(ny, ly, order), Ix)
+    Lap = sp.kron(Iy, second_derivative_1d(nx, lx, order, up)) + \
+        sp.kron(second_derivative_1d(ny, ly, order, up), Ix)
+    Dx = sp.kron(Iy, first_derivative_1d(nx, lx, order, up, cx))
+    Dy = sp.kron(first_derivative_1d(ny, ly, order, up, cy), Ix)
     return Lap.tocsr(), Dx.tocsr(), Dy.tocsr()
 
 

@@ -1,13 +1,14 @@
 """Pins of the CPU oracle against the paper, closed forms, textbook special
 cases, invariants and brute force (CPU only)."""
 import math
+from fractions import Fraction
 
 import numpy as np
 import pytest
 import scipy.sparse.linalg as spla
 
-from conftest import read_golden
-from oracle import alpha_rule, collocation, fourier, operators, paradiag, sequential
+from conftest import golden_path, read_golden
+from oracle import alpha_rule, collocation, fourier, operators, paradiag, sequential, stencils
 from paper_2103_12571_gb300 import workloads
 
 
@@ -132,20 +133,103 @@ def test_stencil_symbol_is_eigenvalue(order, dim):
         np.testing.assert_allclose(A @ e, s * e, atol=1e-9 * max(1, abs(s)))
 
 
-def test_stencil_consistency_with_derivatives():
-    # order-p central differences of sin(2 pi x): error O(h^p)
-    for order in (2, 4):
-        errs = []
-        for n in (32, 64):
-            x = np.arange(n) / n
-            D1 = operators.first_derivative_1d(n, order=order)
-            D2 = operators.second_derivative_1d(n, order=order)
-            f = np.sin(2 * np.pi * x)
-            errs.append((np.max(np.abs(D1 @ f - 2 * np.pi * np.cos(2 * np.pi * x))),
-                         np.max(np.abs(D2 @ f + 4 * np.pi ** 2 * f))))
-        for i in range(2):
-            rate = math.log2(errs[0][i] / errs[1][i])
-            assert abs(rate - order) < 0.1
+def _fd_table():
+    rows = []
+    with open(golden_path("fd_weights.txt")) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            kind, deriv, order, lo, den, *nums = line.split()
+            lo, den = int(lo), int(den)
+            w = {lo + j: Fraction(int(v), den) for j, v in enumerate(nums) if int(v) != 0}
+            rows.append((kind, int(deriv), int(order), w))
+    return rows
+
+
+def test_fd_weights_match_textbook_tables():
+    rows = _fd_table()
+    assert len(rows) == 11
+    for kind, deriv, order, w in rows:
+        if kind == "central":
+            got = stencils.d1_weights(order) if deriv == 1 else stencils.d2_weights(order)
+        else:
+            got = stencils.d1_weights(order, upwind=True, c=1.0)
+        assert got == w, (kind, deriv, order)
+
+
+def _rate(op, f, df, ns=(64, 128)):
+    errs = []
+    for n in ns:
+        x = np.arange(n) / n
+        errs.append(np.max(np.abs(op(n) @ f(x) - df(x))))
+    return math.log2(errs[0] / errs[1])
+
+
+@pytest.mark.parametrize("order", [2, 4, 6])
+def test_central_stencils_converge_at_their_order(order):
+    f = lambda x: np.sin(2 * np.pi * x) + 0.3 * np.cos(6 * np.pi * x)
+    df = lambda x: 2 * np.pi * np.cos(2 * np.pi * x) - 1.8 * np.pi * np.sin(6 * np.pi * x)
+    d2f = lambda x: -4 * np.pi ** 2 * np.sin(2 * np.pi * x) - 10.8 * np.pi ** 2 * np.cos(6 * np.pi * x)
+    ns = (32, 64)
+    assert abs(_rate(lambda n: operators.first_derivative_1d(n, order=order), f, df, ns) - order) < 0.15
+    assert abs(_rate(lambda n: operators.second_derivative_1d(n, order=order), f, d2f, ns) - order) < 0.15
+
+
+@pytest.mark.parametrize("order", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("c", [1.0, -0.5])
+def test_upwind_stencils_converge_at_their_order(order, c):
+    f = lambda x: np.sin(2 * np.pi * x) + 0.3 * np.cos(6 * np.pi * x)
+    df = lambda x: 2 * np.pi * np.cos(2 * np.pi * x) - 1.8 * np.pi * np.sin(6 * np.pi * x)
+    ns = (64, 128) if order < 4 else (32, 64)
+    rate = _rate(lambda n: operators.first_derivative_1d(n, order=order, upwind=True, c=c), f, df, ns)
+    assert abs(rate - order) < 0.2
+
+
+@pytest.mark.parametrize("order", [1, 2, 3, 4, 5])
+def test_upwind_mirror_and_dissipation(order):
+    """For c < 0 the stencil is the mirror image: D(c<0) = -D(c>0)^T.  The
+    upwind operator A = -c D is dissipative for either sign: every
+    eigenvalue has Re <= 0, with Re < 0 on all modes but k = 0."""
+    n = 24
+    Dp = operators.first_derivative_1d(n, order=order, upwind=True, c=1.0).toarray()
+    Dm = operators.first_derivative_1d(n, order=order, upwind=True, c=-2.0).toarray()
+    np.testing.assert_array_equal(Dm, -Dp.T)
+    for c, D in ((1.0, Dp), (-2.0, Dm)):
+        lam = np.linalg.eigvals(-c * D)
+        assert np.all(lam.real <= 1e-10 * n)
+        assert np.sum(lam.real > -1e-8) == 1
+        # symbol = eigenvalues on the Fourier modes
+        prob = dict(dim=1, nx=n, ny=1, nu=0.0, cx=c, cy=0.0, order=order, upwind=True)
+        sig = fourier.symbol(prob)
+        e = np.exp(2j * np.pi * 5 * np.arange(n) / n)
+        np.testing.assert_allclose(-c * D @ e, sig[5] * e, atol=1e-10 * n)
+
+
+def test_central_symbols_closed_forms():
+    """Central symbols: i sin(t)/h, i (8 sin t - sin 2t)/(6h),
+    i (45 sin t - 9 sin 2t + sin 3t)/(30h); (2 cos t - 2)/h^2,
+    (-2 cos 2t + 32 cos t - 30)/(12 h^2),
+    (4 cos 3t - 54 cos 2t + 540 cos t - 490)/(180 h^2), t = 2 pi k / n."""
+    n, L = 40, 2.0
+    h = L / n
+    t = 2 * np.pi * np.arange(n) / n
+    d1 = {2: 1j * np.sin(t) / h, 4: 1j * (8 * np.sin(t) - np.sin(2 * t)) / (6 * h),
+          6: 1j * (45 * np.sin(t) - 9 * np.sin(2 * t) + np.sin(3 * t)) / (30 * h)}
+    d2 = {2: (2 * np.cos(t) - 2) / h ** 2, 4: (-2 * np.cos(2 * t) + 32 * np.cos(t) - 30) / (12 * h ** 2),
+          6: (4 * np.cos(3 * t) - 54 * np.cos(2 * t) + 540 * np.cos(t) - 490) / (180 * h ** 2)}
+    for p in (2, 4, 6):
+        np.testing.assert_allclose(fourier.symbol_d1(n, L, p), d1[p], atol=1e-12 / h)
+        np.testing.assert_allclose(fourier.symbol_d2(n, L, p), d2[p], atol=1e-12 / h ** 2)
+
+
+def test_upwind_problem_laplacian_order():
+    # the Laplacian beside an order-p upwind derivative is centred of order p rounded up to even
+    assert [stencils.laplacian_order(p, True) for p in (1, 2, 3, 4, 5)] == [2, 2, 4, 4, 6]
+    with pytest.raises(ValueError):
+        stencils.check_scheme(6, True)
+    with pytest.raises(ValueError):
+        stencils.check_scheme(3, False)
 
 
 # ------------------------------------------------------ sequential = C^{-1} w
@@ -438,3 +522,39 @@ def test_forced_collocation_converges_at_order_2M_minus_1(M):
         errs.append(np.max(np.abs(u[-1, -1] - g * phi)))
     rates = [math.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
     assert abs(rates[-1] - (2 * M - 1)) < 0.4, (rates, errs)
+
+
+# --------------------------------------------- the paper's advection test
+def _advection_error(N, order, M, L, T, dim=2):
+    """max |u_L,M - u(T)| of the collocation stepping (Fourier closed form)
+    for eq. (advection), u_t + u_x (+ u_y) = 0 with the upwind stencil, against
+    its exact solution sin(2 pi (x - t)) (sin(2 pi (y - t)))."""
+    prob = workloads.problem(dim, N, N, nu=0.0, cx=1.0, cy=1.0 if dim == 2 else 0.0, order=order,
+                             M=M, L=L, T=T, upwind=True)
+    Q = collocation.collocation_matrix(collocation.radau_iia_nodes(M))
+    x = np.arange(N) / N
+    if dim == 2:
+        u0 = np.outer(np.sin(2 * np.pi * x), np.sin(2 * np.pi * x)).reshape(-1)
+        ex = np.outer(np.sin(2 * np.pi * (x - T)), np.sin(2 * np.pi * (x - T))).reshape(-1)
+    else:
+        u0, ex = np.sin(2 * np.pi * x), np.sin(2 * np.pi * (x - T))
+    u = fourier.modal_solution(u0, prob, Q, T / L, L, blocks=[(L - 1, M - 1)])[(L - 1, M - 1)]
+    return np.max(np.abs(u - ex))
+
+
+@pytest.mark.parametrize("tol,N,order,M,L", [(1e-5, 350, 2, 2, 8), (1e-9, 350, 4, 2, 16), (1e-12, 600, 5, 3, 32)])
+def test_table1_advection_parameters_reach_their_tolerance(tol, N, order, M, L):
+    """Table 1 (advection, T = 1e-2): with the chosen N, upwind order, M and L
+    the sequential solution is within tol of the exact one.  A pin of the
+    upwind reading: a wrong bias or order misses these tolerances."""
+    err = _advection_error(N, order, M, L, 1e-2)
+    assert err < tol
+    assert err > tol / 1000      # the paper did not over-resolve (Sec. 5)
+
+
+def test_fig1_advection_setup_reaches_1e_12():
+    """Sec. 5.1 (Fig. 1): T = 0.0128, L = 64, M = 3, 5th-order upwind,
+    N = 700, chosen so that the error is below 1e-12."""
+    assert _advection_error(700, 5, 3, 64, 0.0128) < 1e-12
+    # a 1st-order upwind stencil on the same grid misses it by far
+    assert _advection_error(700, 1, 3, 64, 0.0128, dim=1) > 1e-6
