@@ -116,8 +116,9 @@ def fp64_flops_per_dof(M, taps):
     return (1 + 2 * (taps - 1)) + 2 * M + 2 + 1.0 / M
 
 
-KERNEL_SOURCES = ["paper_2103_12571_gb300/csrc/k_time.cu", "paper_2103_12571_gb300/csrc/fft.cuh",
-                  "paper_2103_12571_gb300/csrc/common.cuh", "paper_2103_12571_gb300/csrc/k_space.cu"]
+KERNEL_SOURCES = ["paper_2103_12571_gb300/csrc/k_time.cuh", "paper_2103_12571_gb300/csrc/k_upd.cu",
+                  "paper_2103_12571_gb300/csrc/fft.cuh", "paper_2103_12571_gb300/csrc/common.cuh",
+                  "paper_2103_12571_gb300/csrc/k_space.cu"]
 
 
 def source_hash():

@@ -47,6 +47,8 @@ extern "C" {
 
 #define AC_INNER_FFT      0  /* exact spatial-FFT solve of eq. (d2)                    */
 #define AC_INNER_BICGSTAB 1  /* batched BiCGStab on the stencil, relative tolerance tau */
+#define AC_INNER_GMRES    2  /* batched restarted GMRES(m) on the stencil, unpreconditioned,
+                                relative tolerance tau (the paper's inner solver, Sec. 4.1) */
 
 #define AC_ALPHA_FIXED 0  /* alpha_k = alpha0 for every k                                 */
 #define AC_ALPHA_PAPER 1  /* Algorithm 2: alpha_{k+1} = sqrt(gamma/m_k), m_{k+1} = 2 sqrt(m_k gamma) */
@@ -63,16 +65,27 @@ extern "C" {
 #define AC_MAX_STATS 128
 
 /* Spatial operator A = nu * Lap_h - cx * D_x - cy * D_y on the periodic box
- * [0,lx) x [0,ly) with nx (x ny) points, central differences of order 2 or 4
- * (Sec. 5 uses periodic central/upwind stencils; the standard central
- * coefficients are used here).  dim = 1 ignores ny, ly, cy. */
+ * [0,lx) x [0,ly) with nx (x ny) points and h = length / n per axis.  Sec. 5
+ * discretises the heat equation with centred and the advection equation
+ * with upwind periodic stencils, of the orders in Tables 1-2; the paper
+ * prints no weights, so the standard finite-difference formulas are used
+ * (the weights exact on polynomials of degree <= number of points - 1):
+ *   upwind = 0: centred first and second derivatives of order 2, 4 or 6
+ *               (offsets -order/2 .. order/2);
+ *   upwind = 1: first derivative of order 1..5 on the offsets lo .. lo+order,
+ *               lo = -(order/2 + 1) (integer division), for a positive
+ *               velocity component, mirrored (w(o) -> -w(-o)) for a negative
+ *               one; the Laplacian is the centred one of the order rounded
+ *               up to even.
+ * The stencil radius is at most 3.  dim = 1 ignores ny, ly, cy. */
 typedef struct {
     int dim;          /* 1 or 2                                     */
     int nx, ny;       /* grid points per axis (powers of two for AC_INNER_FFT) */
     double lx, ly;    /* box lengths                                */
     double nu;        /* diffusion coefficient                      */
     double cx, cy;    /* advection velocity                         */
-    int order;        /* 2 or 4                                     */
+    int order;        /* centred: 2, 4, 6; upwind: 1..5             */
+    int upwind;       /* 0: centred first derivative, 1: upwind     */
 } ac_problem;
 
 /* Choice of alpha_k per iteration (Sec. 3.3). */
@@ -84,8 +97,10 @@ typedef struct {
     double tau;       /* inner-solve relative tolerance (BiCGStab), used in gamma too */
     int max_iter;     /* outer iteration cap (<= AC_MAX_STATS)                        */
     int stop_rule;    /* AC_STOP_RESIDUAL | AC_STOP_PAPER                             */
-    int inner_max_iter; /* BiCGStab iteration cap per system (<= 0: 4000)             */
+    int inner_max_iter; /* Krylov iteration cap per system (<= 0: 4000); for GMRES the
+                           Arnoldi steps over all restarts                              */
     int form;           /* AC_FORM_CORRECTION | AC_FORM_PAPER                           */
+    int inner_restart;  /* GMRES restart length m, 1..32 (<= 0: 30)                     */
 } ac_alpha_schedule;
 
 /* Per-solve record (host memory, filled by the solve calls). */
@@ -97,8 +112,8 @@ typedef struct {
     double alpha[AC_MAX_STATS];       /* alpha_{k+1} used in iteration k                */
     double m[AC_MAX_STATS];           /* Algorithm 2's m_k (0 for other modes)          */
     double diff_last[AC_MAX_STATS];   /* ||u_L^{(k+1)} - u_L^{(k)}||_inf                 */
-    int inner_iters[AC_MAX_STATS];    /* BiCGStab: max iterations over systems, per k   */
-    int inner_failed[AC_MAX_STATS];   /* BiCGStab: systems that stopped above tau, per k */
+    int inner_iters[AC_MAX_STATS];    /* Krylov inner solver: max iterations over systems, per k */
+    int inner_failed[AC_MAX_STATS];   /* Krylov inner solver: systems that stopped above tau, per k */
     double w_norm2;                   /* ||w||_2                                         */
     double w_inf;                     /* ||w||_inf                                       */
 } ac_stats;
@@ -107,7 +122,8 @@ typedef struct {
 typedef struct {
     int N, M, L, F;                   /* F = L/2 + 1 stored time frequencies            */
     int tile_fwd, tile_upd;           /* grid points per CTA in the time kernels        */
-    int spatial_path;                 /* 0: 1D one CTA per plane, 1: 2D one CTA per plane, 2: 2D three passes, 3: BiCGStab */
+    int spatial_path;                 /* 0: 1D one CTA per plane, 1: 2D one CTA per plane, 2: 2D three passes,
+                                         3: BiCGStab, 4: GMRES                                               */
     long long workspace_bytes;        /* device memory owned by the plan               */
     long long launches;               /* kernels launched by this plan so far          */
 } ac_plan_info;
@@ -191,6 +207,20 @@ int ac_window_solve(ac_plan* plan, const double* u0, int n_windows, double* u_en
                     double* work, double tol, ac_stats* stats, int* iters_total,
                     void* stream);
 
+/* Sequential collocation stepping, the baseline of Sec. 4.2 (T_Mpar): the
+ * L steps of eq. (collocation) one after another, each solved by
+ * diagonalising Q = S diag(lambda) S^{-1}: z = (S^{-1} x I)(1 x u_{l-1,M} + v_l),
+ * the M shifted spatial solves (I - dT lambda_m A) z_m = z_m with the plan's
+ * inner solver (in parallel over m), and u_l = Re (S x I) z.  It computes the
+ * same u as ac_richardson_solve (the solution of eq. (globalsys)) without
+ * iterating; in complex64 plans the solves carry complex64 rounding.
+ * u0: device, N doubles.  b: device, L*M*N doubles (the collocation right-hand
+ * side v of ac_collocation_rhs) or NULL.  u: device, L*M*N doubles, output,
+ * distinct from u0 and b.  The L steps are captured once into a CUDA graph
+ * per (u0, b, u) triple and replayed on `stream`; the Krylov inner solvers'
+ * per-system status is not reported here.  Not thread-safe per plan. */
+int ac_sequential_solve(ac_plan* plan, const double* u0, const double* b, double* u, void* stream);
+
 /* ---- adjoint (not in the paper; derived from eq. (globalsys)) ----------- */
 
 /* lam = C^{-T} g.  Reversing the time index turns C^T into a system of the
@@ -254,6 +284,14 @@ int ac_collocation_matrix(int M, double* Q);
  * Returns AC_ERR_NOT_DIAGONALIZABLE if some cond(S_f) > 1e10. */
 int ac_freq_tables(int M, int L, double alpha, int transposed,
                    double* mu, double* Sinv, double* P, double* cond);
+
+/* Per-axis stencil taps of A on the offsets -3..3 (index offset + 3), the
+ * weights of the scheme above scaled by nu / h^2 and -c / h:  A u at grid
+ * point (ix, iy) = sum_o tx[o+3] u(ix+o, iy) + ty[o+3] u(ix, iy+o).
+ * tx, ty: host, 7 doubles each (ty zero in 1D).  rad: host int, the largest
+ * |o| with a nonzero tap of either axis (may be NULL).  Returns
+ * AC_ERR_INVALID_ARG for an unsupported scheme. */
+int ac_stencil_taps(const ac_problem* prob, double* tx, double* ty, int* rad);
 
 /* Algorithm 2's sequence: alphas[k] = alpha_{k+1}, ms[k] = m_k (ms[0] = m0),
  * k = 0..n-1 (ms has n+1 entries). */

@@ -19,7 +19,7 @@ AC_ERR_CUDA = -5
 AC_ERR_NOT_FINITE = -6
 
 AC_C128, AC_C64 = 0, 1
-AC_INNER_FFT, AC_INNER_BICGSTAB = 0, 1
+AC_INNER_FFT, AC_INNER_BICGSTAB, AC_INNER_GMRES = 0, 1, 2
 AC_ALPHA_FIXED, AC_ALPHA_PAPER, AC_ALPHA_MIXED = 0, 1, 2
 AC_STOP_RESIDUAL, AC_STOP_PAPER = 0, 1
 AC_FORM_CORRECTION, AC_FORM_PAPER = 0, 1
@@ -29,13 +29,14 @@ AC_MAX_STATS = 128
 class Problem(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
                 ("lx", ctypes.c_double), ("ly", ctypes.c_double), ("nu", ctypes.c_double),
-                ("cx", ctypes.c_double), ("cy", ctypes.c_double), ("order", ctypes.c_int)]
+                ("cx", ctypes.c_double), ("cy", ctypes.c_double), ("order", ctypes.c_int),
+                ("upwind", ctypes.c_int)]
 
 
 class Schedule(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int), ("alpha0", ctypes.c_double), ("m0", ctypes.c_double),
                 ("tau", ctypes.c_double), ("max_iter", ctypes.c_int), ("stop_rule", ctypes.c_int),
-                ("inner_max_iter", ctypes.c_int), ("form", ctypes.c_int)]
+                ("inner_max_iter", ctypes.c_int), ("form", ctypes.c_int), ("inner_restart", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -71,7 +72,9 @@ _PROTOS = {
     "ac_window_solve": (_I, [_P, _P, _I, _P, _P, _D, ctypes.POINTER(Stats), ctypes.POINTER(_I), _P]),
     "ac_grad_params": (_I, [_P, _P, _P, _P, _P, _P]),
     "ac_precond_solve_noalloc": (_I, [ctypes.POINTER(Problem), _I, _I, _D, _D, _I, _P, _P, _P]),
+    "ac_sequential_solve": (_I, [_P, _P, _P, _P, _P]),
     "ac_radau_nodes": (_I, [_I, _P]),
+    "ac_stencil_taps": (_I, [ctypes.POINTER(Problem), _P, _P, _P]),
     "ac_collocation_matrix": (_I, [_I, _P]),
     "ac_freq_tables": (_I, [_I, _I, _D, _I, _P, _P, _P, _P]),
     "ac_alpha_sequence": (_I, [_D, _D, _I, _P, _P]),

@@ -30,11 +30,12 @@ def make_problem(prob):
     return C.Problem(dim=int(prob["dim"]), nx=int(prob["nx"]), ny=int(prob.get("ny", 1)),
                      lx=float(prob.get("lx", 1.0)), ly=float(prob.get("ly", 1.0)),
                      nu=float(prob.get("nu", 0.0)), cx=float(prob.get("cx", 0.0)),
-                     cy=float(prob.get("cy", 0.0)), order=int(prob.get("order", 2)))
+                     cy=float(prob.get("cy", 0.0)), order=int(prob.get("order", 2)),
+                     upwind=int(bool(prob.get("upwind", False))))
 
 
 PRECISION = {"c128": C.AC_C128, "fp64": C.AC_C128, "c64": C.AC_C64, "mixed": C.AC_C64}
-INNER = {"fft": C.AC_INNER_FFT, "bicgstab": C.AC_INNER_BICGSTAB}
+INNER = {"fft": C.AC_INNER_FFT, "bicgstab": C.AC_INNER_BICGSTAB, "gmres": C.AC_INNER_GMRES}
 ALPHA = {"fixed": C.AC_ALPHA_FIXED, "paper": C.AC_ALPHA_PAPER, "mixed": C.AC_ALPHA_MIXED}
 STOP = {"residual": C.AC_STOP_RESIDUAL, "paper": C.AC_STOP_PAPER}
 FORM = {"correction": C.AC_FORM_CORRECTION, "paper": C.AC_FORM_PAPER}
@@ -53,7 +54,7 @@ class Plan:
 
     def __init__(self, prob, M=None, L=None, dT=None, precision="c128", inner="fft", alpha="paper",
                  alpha0=1e-4, m0=0.0, tau=0.0, max_iter=50, stop="residual", inner_max_iter=0,
-                 form="correction"):
+                 form="correction", inner_restart=0):
         M = int(M if M is not None else prob["M"])
         L = int(L if L is not None else prob["L"])
         dT = float(dT if dT is not None else prob["T"] / L)
@@ -62,7 +63,7 @@ class Plan:
         self.prob = dict(prob)
         sched = C.Schedule(mode=ALPHA[alpha], alpha0=float(alpha0), m0=float(m0), tau=float(tau),
                            max_iter=int(max_iter), stop_rule=STOP[stop], inner_max_iter=int(inner_max_iter),
-                           form=FORM[form])
+                           form=FORM[form], inner_restart=int(inner_restart))
         handle = ctypes.c_void_p()
         C.check(C.lib().ac_setup(ctypes.byref(make_problem(prob)), M, L, dT, ctypes.byref(sched),
                                  PRECISION[precision], INNER[inner], ctypes.byref(handle)), "ac_setup")
@@ -140,6 +141,14 @@ class Plan:
                                         ctypes.byref(st), ctypes.byref(tot), _stream()), "ac_window_solve")
         return u_end, tot.value, stats_dict(st)
 
+    def sequential_solve(self, u0, b=None, out=None):
+        """The L steps one after another by diagonalisation of Q (the
+        paper's sequential baseline), replayed from a CUDA graph."""
+        out = self.empty() if out is None else out
+        C.check(C.lib().ac_sequential_solve(self._h, _ptr(u0), _ptr(b), _ptr(out), _stream()),
+                "ac_sequential_solve")
+        return out
+
     def adjoint_solve(self, g, tol, lam=None, raise_on_fail=True):
         lam = self.empty() if lam is None else lam
         st = C.Stats()
@@ -173,6 +182,15 @@ def radau_nodes(M):
     t = np.zeros(M)
     C.check(C.lib().ac_radau_nodes(M, t.ctypes.data_as(ctypes.c_void_p)), "ac_radau_nodes")
     return t
+
+
+def stencil_taps(prob):
+    """(tx, ty, rad): per-axis taps of A on the offsets -3..3 (index o + 3)."""
+    tx, ty, rad = np.zeros(7), np.zeros(7), ctypes.c_int(0)
+    pr = make_problem(prob)
+    C.check(C.lib().ac_stencil_taps(ctypes.byref(pr), tx.ctypes.data_as(ctypes.c_void_p),
+                                    ty.ctypes.data_as(ctypes.c_void_p), ctypes.byref(rad)), "ac_stencil_taps")
+    return tx, ty, rad.value
 
 
 def collocation_matrix(M):

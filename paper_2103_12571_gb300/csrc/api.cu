@@ -72,7 +72,7 @@ struct ac_plan {
     // host data
     double t[8], Q[64];
     ac::Grid grid_fwd, grid_adj;  // A and A^T
-    double d1x[5], d2x[5], d1y[5], d2y[5];
+    double d1x[7], d2x[7], d1y[7], d2y[7];   // derivative weights / h, / h^2 on offsets -3..3
     // device buffers
     void* X = nullptr;
     void* tw_L = nullptr;
@@ -94,10 +94,9 @@ struct ac_plan {
     double* d_part_d = nullptr;  // FP64 reductions
     double* d_dtQ = nullptr;     // dT Q
     double* d_dtQT = nullptr;    // dT Q^T
-    void* d_bicg = nullptr;      // BiCGStab vectors when they do not fit in shared memory
-    int* d_iters = nullptr;      // BiCGStab iterations per system
+    void* d_bicg = nullptr;      // Krylov vectors when they do not fit in shared memory
+    int* d_iters = nullptr;      // Krylov iterations per system
     int* h_iters = nullptr;      // pinned copy
-    bool iters_pending = false;
     float* h_part_fwd = nullptr;  // pinned
     float* h_part_upd = nullptr;
     double* h_part_d = nullptr;
@@ -109,6 +108,14 @@ struct ac_plan {
     long long workspace = 0;
     long long launches = 0;
     cudaEvent_t ev_res = nullptr;
+    // sequential stepping by diagonalisation of Q (ac_sequential_solve)
+    double* d_seq_S = nullptr;      // [M][M] complex S, Q = S diag(lambda) S^{-1}
+    double* d_seq_Sinv = nullptr;   // [M][M] complex S^{-1}
+    void* d_seq_mu = nullptr;       // [M] complex dT * lambda_m, transform precision
+    cudaStream_t seq_capture = nullptr;
+    cudaGraphExec_t seq_exec = nullptr;
+    const void* seq_key[3] = {nullptr, nullptr, nullptr};
+    long long seq_launches = 0;     // kernels per replay of the graph
     // profiling
     bool prof = false;
     std::vector<EventPair> pending;
@@ -235,10 +242,83 @@ static int ensure_tables(ac_plan* p, double alpha, int transposed, double wscale
 // Relative tolerance of the BiCGStab inner solves: the schedule's tau (1e-8
 // if unset), floored at 2^-20 in the complex64 form, where FP32 arithmetic
 // cannot certify a smaller relative residual.
+static int gmres_restart(const ac_plan* p) {
+    const int m = p->sched.inner_restart > 0 ? p->sched.inner_restart : 30;
+    return std::min(m, 32);
+}
+
 static double inner_tau(const ac_plan* p) {
     double tau = p->sched.tau > 0 ? p->sched.tau : 1e-8;
     if (p->precision == AC_C64) tau = std::max(tau, std::ldexp(1.0, -20));
     return tau;
+}
+
+// The shifted spatial solves of eq. (d2), (I - mu dT A) x = X_plane, in place
+// on `planes` planes of N complex values with per-plane shifts mu_dT, by the
+// plan's inner solver.  fetch_iters: copy the Krylov iteration counts to the
+// host (a stream-ordered copy; off inside graph capture).
+template <typename R>
+static int run_spatial(ac_plan* p, void* X, const void* mu_dT, int planes, int transposed, bool fetch_iters,
+                       cudaStream_t st) {
+    ac::SpaceArgs sa{};
+    sa.nx = p->prob.nx;
+    sa.ny = p->prob.dim == 2 ? p->prob.ny : 1;
+    sa.lognx = ilog2(sa.nx);
+    sa.logny = ilog2(sa.ny);
+    sa.planes = planes;
+    sa.M = p->M;
+    sa.X = X;
+    sa.mu_dT = mu_dT;
+    sa.sig_x = transposed ? p->sigT_x : p->sig_x;
+    sa.sig_y = transposed ? p->sigT_y : p->sig_y;
+    sa.tw_x = p->tw_x;
+    sa.tw_y = p->tw_y;
+    sa.rows_per_block = p->rows_per_block;
+    sa.cols_per_block = p->cols_per_block;
+    if (p->spatial_path == 0) {
+        CK(ac::launch_space_1d<R>(sa, st));
+        p->launches++;
+    } else if (p->spatial_path == 1) {
+        CK(ac::launch_space_2d_small<R>(sa, st));
+        p->launches++;
+    } else if (p->spatial_path == 2) {
+        CK(ac::launch_space_rows<R>(sa, 0, st));
+        CK(ac::launch_space_cols<R>(sa, st));
+        CK(ac::launch_space_rows<R>(sa, 1, st));
+        p->launches += 3;
+    } else if (p->spatial_path == 3) {
+        ac::BicgArgs ba{};
+        ba.g = transposed ? p->grid_adj : p->grid_fwd;
+        ba.planes = planes;
+        ba.M = p->M;
+        ba.max_iter = p->sched.inner_max_iter > 0 ? p->sched.inner_max_iter : 4000;
+        ba.tau = inner_tau(p);
+        ba.X = X;
+        ba.mu_dT = mu_dT;
+        ba.iters = p->d_iters;
+        CK(ac::launch_bicgstab<R>(ba, p->d_bicg, st));
+        p->launches++;
+        if (fetch_iters)
+            CK(cudaMemcpyAsync(p->h_iters, p->d_iters, sizeof(int) * planes, cudaMemcpyDeviceToHost, st));
+    } else if (p->spatial_path == 4) {
+        ac::GmresArgs ga{};
+        ga.g = transposed ? p->grid_adj : p->grid_fwd;
+        ga.planes = planes;
+        ga.M = p->M;
+        ga.max_iter = p->sched.inner_max_iter > 0 ? p->sched.inner_max_iter : 4000;
+        ga.restart = gmres_restart(p);
+        ga.tau = inner_tau(p);
+        ga.X = X;
+        ga.mu_dT = mu_dT;
+        ga.iters = p->d_iters;
+        CK(ac::launch_gmres<R>(ga, p->d_bicg, st));
+        p->launches++;
+        if (fetch_iters)
+            CK(cudaMemcpyAsync(p->h_iters, p->d_iters, sizeof(int) * planes, cudaMemcpyDeviceToHost, st));
+    } else {
+        return fail(AC_ERR_INVALID_ARG, "inner solver path %d not available", p->spatial_path);
+    }
+    return AC_OK;
 }
 
 // ------------------------------------------------------ one preconditioner
@@ -278,51 +358,10 @@ static int stage_a(ac_plan* p, const double* u, const double* u0, const double* 
         CK(cudaEventRecord(p->ev_res, st));
     }
     if (fwd_only) return AC_OK;
-    ac::SpaceArgs sa{};
-    sa.nx = p->prob.nx;
-    sa.ny = p->prob.dim == 2 ? p->prob.ny : 1;
-    sa.lognx = ilog2(sa.nx);
-    sa.logny = ilog2(sa.ny);
-    sa.planes = p->F * p->M;
-    sa.M = p->M;
-    sa.X = p->X;
-    sa.mu_dT = p->d_mu;
-    sa.sig_x = transposed ? p->sigT_x : p->sig_x;
-    sa.sig_y = transposed ? p->sigT_y : p->sig_y;
-    sa.tw_x = p->tw_x;
-    sa.tw_y = p->tw_y;
-    sa.rows_per_block = p->rows_per_block;
-    sa.cols_per_block = p->cols_per_block;
     {
         ProfScope ps(p, KK_SPACE, st);
-        if (p->spatial_path == 0) {
-            CK(ac::launch_space_1d<R>(sa, st));
-            p->launches++;
-        } else if (p->spatial_path == 1) {
-            CK(ac::launch_space_2d_small<R>(sa, st));
-            p->launches++;
-        } else if (p->spatial_path == 2) {
-            CK(ac::launch_space_rows<R>(sa, 0, st));
-            CK(ac::launch_space_cols<R>(sa, st));
-            CK(ac::launch_space_rows<R>(sa, 1, st));
-            p->launches += 3;
-        } else if (p->spatial_path == 3) {
-            ac::BicgArgs ba{};
-            ba.g = transposed ? p->grid_adj : p->grid_fwd;
-            ba.planes = p->F * p->M;
-            ba.M = p->M;
-            ba.max_iter = p->sched.inner_max_iter > 0 ? p->sched.inner_max_iter : 4000;
-            ba.tau = inner_tau(p);
-            ba.X = p->X;
-            ba.mu_dT = p->d_mu;
-            ba.iters = p->d_iters;
-            CK(ac::launch_bicgstab<R>(ba, p->d_bicg, st));
-            p->launches++;
-            CK(cudaMemcpyAsync(p->h_iters, p->d_iters, sizeof(int) * ba.planes, cudaMemcpyDeviceToHost, st));
-            p->iters_pending = true;
-        } else {
-            return fail(AC_ERR_INVALID_ARG, "inner solver path %d not available", p->spatial_path);
-        }
+        int rc = run_spatial<R>(p, p->X, p->d_mu, p->F * p->M, transposed, true, st);
+        if (rc) return rc;
     }
     return AC_OK;
 }
@@ -422,8 +461,8 @@ static int a_u0_inf(ac_plan* p, const double* u0, int transposed, double* out, c
 
 static double a_inf_norm(const ac_plan* p) {
     double s = 0.0;
-    for (int i = 0; i < 5; ++i) {
-        if (i == 2) continue;
+    for (int i = 0; i < 7; ++i) {
+        if (i == 3) continue;
         s += std::fabs(p->grid_fwd.tx[i]) + (p->prob.dim == 2 ? std::fabs(p->grid_fwd.ty[i]) : 0.0);
     }
     return s + std::fabs(p->grid_fwd.c0);
@@ -476,7 +515,7 @@ static int richardson_loop(ac_plan* p, const double* u0, const double* b, int b_
     const ac_alpha_schedule& sc = p->sched;
     const int max_iter = std::min(std::max(sc.max_iter, 1), AC_MAX_STATS - 1);
     const double eps = p->precision == AC_C128 ? std::ldexp(1.0, -53) : std::ldexp(1.0, -24);
-    const double tau = p->inner == AC_INNER_BICGSTAB ? inner_tau(p) : 0.0;
+    const double tau = p->inner != AC_INNER_FFT ? inner_tau(p) : 0.0;
     const double gam = p->L * (3.0 * eps + tau) * winf;
     // m0 ~ ||u^(0) - u*||_inf: T max|u_t(0)| = T ||A u0 + b||_inf (Sec. 3.3, the
     // Lipschitz estimate) when the caller gives none; for a zero initial
@@ -559,7 +598,7 @@ static int richardson_loop(ac_plan* p, const double* u0, const double* b, int b_
         rc = precond_a(p, u, u0, b, b_rev, transposed, st, true);
         if (rc) return rc;
         CK(cudaEventSynchronize(p->ev_res));
-        if (k > 0 && p->spatial_path == 3) S->inner_iters[k - 1] = inner_summary(p, &S->inner_failed[k - 1]);
+        if (k > 0 && p->spatial_path >= 3) S->inner_iters[k - 1] = inner_summary(p, &S->inner_failed[k - 1]);
         double s = 0.0;
         for (int i = 0; i < p->grid; ++i) s += p->h_part_fwd[i];
         const double res = std::sqrt(s) * wscale / wn2;
@@ -602,6 +641,44 @@ static int richardson_loop(ac_plan* p, const double* u0, const double* b, int b_
 }
 
 // --------------------------------------------------------------- C ABI
+// ------------------------------------------- sequential stepping (baseline)
+static int ensure_seq_tables(ac_plan* p, cudaStream_t st) {
+    if (p->d_seq_S) return AC_OK;
+    const int M = p->M;
+    std::vector<cd> B((size_t)M * M), lam(M), S((size_t)M * M), Sinv((size_t)M * M);
+    for (int i = 0; i < M * M; ++i) B[i] = p->Q[i];
+    const double c = ac::eig_small(M, B.data(), lam.data(), S.data(), Sinv.data());
+    if (c < 0 || c > 1e10) return fail(AC_ERR_NOT_DIAGONALIZABLE, "Q is not diagonalisable (cond %g)", c);
+    for (auto& v : lam) v *= p->dT;
+    cudaError_t e = cudaMalloc((void**)&p->d_seq_S, sizeof(cd) * M * M);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&p->d_seq_Sinv, sizeof(cd) * M * M);
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_seq_mu, (size_t)M * p->csize);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p->d_seq_S, S.data(), sizeof(cd) * M * M, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(p->d_seq_Sinv, Sinv.data(), sizeof(cd) * M * M, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = upload_c(p, p->d_seq_mu, lam.data(), lam.size(), st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail(AC_ERR_CUDA, "sequential tables: %s", cudaGetErrorString(e));
+    return AC_OK;
+}
+
+// the L steps, launched on st (used inside the graph capture)
+template <typename R>
+static int seq_steps(ac_plan* p, const double* u0, const double* b, double* u, cudaStream_t st) {
+    const long long N = p->N;
+    const int M = p->M;
+    for (int l = 0; l < p->L; ++l) {
+        const double* uprev = l == 0 ? u0 : u + ((size_t)(l - 1) * M + (M - 1)) * N;
+        const double* v = b ? b + (size_t)l * M * N : nullptr;
+        CK(ac::launch_seq_in<R>(M, N, uprev, v, p->d_seq_Sinv, p->X, st));
+        int rc = run_spatial<R>(p, p->X, p->d_seq_mu, M, 0, false, st);
+        if (rc) return rc;
+        CK(ac::launch_seq_out<R>(M, N, p->X, p->d_seq_S, u + (size_t)l * M * N, st));
+        p->launches += 2;
+    }
+    return AC_OK;
+}
+
 extern "C" {
 
 const char* ac_status_string(int s) {
@@ -634,6 +711,10 @@ void ac_destroy(ac_plan* p) {
     if (p->h_part_d) cudaFreeHost(p->h_part_d);
     if (p->h_iters) cudaFreeHost(p->h_iters);
     if (p->ev_res) cudaEventDestroy(p->ev_res);
+    if (p->seq_exec) cudaGraphExecDestroy(p->seq_exec);
+    if (p->seq_capture) cudaStreamDestroy(p->seq_capture);
+    for (void* b : {(void*)p->d_seq_S, (void*)p->d_seq_Sinv, p->d_seq_mu})
+        if (b) cudaFree(b);
     delete p;
 }
 
@@ -642,7 +723,8 @@ int ac_setup(const ac_problem* prob, int M, int L, double dT, const ac_alpha_sch
     if (!prob || !sched || !out) return fail(AC_ERR_INVALID_ARG, "null argument");
     *out = nullptr;
     if (prob->dim != 1 && prob->dim != 2) return fail(AC_ERR_INVALID_ARG, "dim must be 1 or 2");
-    if (prob->order != 2 && prob->order != 4) return fail(AC_ERR_INVALID_ARG, "order must be 2 or 4");
+    if (prob->upwind ? (prob->order < 1 || prob->order > 5) : (prob->order != 2 && prob->order != 4 && prob->order != 6))
+        return fail(AC_ERR_INVALID_ARG, "order must be 2, 4 or 6 (centred) or 1..5 (upwind)");
     const int ny = prob->dim == 2 ? prob->ny : 1;
     if (prob->nx < 2 || ny < 1 || (prob->dim == 2 && ny < 2))
         return fail(AC_ERR_INVALID_ARG, "grid too small");
@@ -650,7 +732,8 @@ int ac_setup(const ac_problem* prob, int M, int L, double dT, const ac_alpha_sch
     if (!is_pow2(L) || L < 2 || L > 1024) return fail(AC_ERR_INVALID_ARG, "L must be a power of two in 2..1024");
     if (!(dT > 0)) return fail(AC_ERR_INVALID_ARG, "dT must be positive");
     if (precision != AC_C128 && precision != AC_C64) return fail(AC_ERR_INVALID_ARG, "bad precision");
-    if (inner != AC_INNER_FFT && inner != AC_INNER_BICGSTAB) return fail(AC_ERR_INVALID_ARG, "bad inner solver");
+    if (inner != AC_INNER_FFT && inner != AC_INNER_BICGSTAB && inner != AC_INNER_GMRES)
+        return fail(AC_ERR_INVALID_ARG, "bad inner solver");
     if (!(prob->lx > 0) || (prob->dim == 2 && !(prob->ly > 0))) return fail(AC_ERR_INVALID_ARG, "bad box length");
     const long long Nll = (long long)prob->nx * ny;
     if (Nll > (1LL << 30)) return fail(AC_ERR_INVALID_ARG, "grid too large");
@@ -672,37 +755,34 @@ int ac_setup(const ac_problem* prob, int M, int L, double dT, const ac_alpha_sch
     ac::radau_nodes(M, p->t);
     ac::collocation_matrix(M, p->t, p->Q);
 
-    // stencil taps of A and A^T
-    double tx[5] = {0}, ty[5] = {0};
-    ac::axis_taps(prob->order, prob->nx, prob->lx, prob->nu, prob->cx, tx);
-    if (prob->dim == 2) ac::axis_taps(prob->order, ny, prob->ly, prob->nu, prob->cy, ty);
+    // stencil taps of A and A^T (A^T: the taps mirrored, o -> -o)
+    ac::Stencil sten;
+    if (!ac::problem_stencil(p->prob, &sten)) {
+        ac_destroy(p);
+        return fail(AC_ERR_INVALID_ARG, "unsupported stencil");
+    }
     ac::Grid g;
     g.dim = prob->dim;
     g.nx = prob->nx;
     g.ny = ny;
     g.N = p->N;
-    g.rad = prob->order == 4 ? 2 : 1;
-    for (int i = 0; i < 5; ++i) {
-        g.tx[i] = tx[i];
-        g.ty[i] = ty[i];
+    g.rad = sten.rad;
+    for (int i = 0; i < 7; ++i) {
+        g.tx[i] = sten.tx[i];
+        g.ty[i] = sten.ty[i];
     }
-    g.c0 = tx[2] + ty[2];
+    g.c0 = sten.tx[3] + sten.ty[3];
     p->grid_fwd = g;
-    for (int i = 0; i < 5; ++i) {
-        g.tx[i] = tx[4 - i];
-        g.ty[i] = ty[4 - i];
+    for (int i = 0; i < 7; ++i) {
+        g.tx[i] = sten.tx[6 - i];
+        g.ty[i] = sten.ty[6 - i];
     }
     p->grid_adj = g;
-    {
-        double d1[5], d2[5];
-        ac::central_coeffs(prob->order, d1, d2);
-        const double hx = prob->lx / prob->nx, hy = prob->dim == 2 ? prob->ly / ny : 1.0;
-        for (int i = 0; i < 5; ++i) {
-            p->d1x[i] = d1[i] / hx;
-            p->d2x[i] = d2[i] / (hx * hx);
-            p->d1y[i] = prob->dim == 2 ? d1[i] / hy : 0.0;
-            p->d2y[i] = prob->dim == 2 ? d2[i] / (hy * hy) : 0.0;
-        }
+    for (int i = 0; i < 7; ++i) {
+        p->d1x[i] = sten.d1x[i];
+        p->d2x[i] = sten.d2x[i];
+        p->d1y[i] = sten.d1y[i];
+        p->d2y[i] = sten.d2y[i];
     }
 
     // spatial solve path
@@ -734,8 +814,8 @@ int ac_setup(const ac_problem* prob, int M, int L, double dT, const ac_alpha_sch
             }
         }
     } else {
-        p->spatial_path = 3;
-        const int rad = prob->order == 4 ? 2 : 1;
+        p->spatial_path = inner == AC_INNER_GMRES ? 4 : 3;
+        const int rad = sten.rad;
         if (prob->nx < 2 * rad + 1 || (prob->dim == 2 && ny < 2 * rad + 1)) {
             ac_destroy(p);
             return fail(AC_ERR_INVALID_ARG, "grid smaller than the stencil");
@@ -788,12 +868,16 @@ int ac_setup(const ac_problem* prob, int M, int L, double dT, const ac_alpha_sch
     if (p->spatial_path == 3) {
         AL(p->d_iters, sizeof(int) * F * M);
         if (6 * cs * (size_t)p->N > 200 * 1024) AL(p->d_bicg, 6 * cs * (size_t)p->N * F * M);
+    } else if (p->spatial_path == 4) {
+        AL(p->d_iters, sizeof(int) * F * M);
+        const size_t per = ac::gmres_vector_bytes(gmres_restart(p), p->N, cs);
+        if (per > 160 * 1024) AL(p->d_bicg, per * F * M);
     }
 #undef AL
     if (e == cudaSuccess) e = cudaMallocHost((void**)&p->h_part_fwd, sizeof(float) * p->grid);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&p->h_part_upd, sizeof(float) * p->grid_upd);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&p->h_part_d, sizeof(double) * p->part_d_len);
-    if (e == cudaSuccess && p->spatial_path == 3) e = cudaMallocHost((void**)&p->h_iters, sizeof(int) * F * M);
+    if (e == cudaSuccess && p->spatial_path >= 3) e = cudaMallocHost((void**)&p->h_iters, sizeof(int) * F * M);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_res, cudaEventDisableTiming);  // spin: low latency
     if (e != cudaSuccess) {
         int rc = fail(AC_ERR_CUDA, "allocation failed: %s", cudaGetErrorString(e));
@@ -955,6 +1039,44 @@ int ac_window_solve(ac_plan* p, const double* u0, int n_windows, double* u_end, 
     return AC_OK;
 }
 
+int ac_sequential_solve(ac_plan* p, const double* u0, const double* b, double* u, void* stream) {
+    if (!p || !u0 || !u || u == u0) return fail(AC_ERR_INVALID_ARG, "bad argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = ensure_seq_tables(p, st);
+    if (rc) return rc;
+    if (!p->seq_exec || p->seq_key[0] != u0 || p->seq_key[1] != b || p->seq_key[2] != u) {
+        if (p->seq_exec) {
+            cudaGraphExecDestroy(p->seq_exec);
+            p->seq_exec = nullptr;
+        }
+        if (!p->seq_capture) CK(cudaStreamCreateWithFlags(&p->seq_capture, cudaStreamNonBlocking));
+        const long long before = p->launches;
+        CK(cudaStreamBeginCapture(p->seq_capture, cudaStreamCaptureModeThreadLocal));
+        rc = p->precision == AC_C128 ? seq_steps<double>(p, u0, b, u, p->seq_capture)
+                                     : seq_steps<float>(p, u0, b, u, p->seq_capture);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(p->seq_capture, &graph);   // always end the capture
+        p->seq_launches = p->launches - before;
+        p->launches = before;
+        if (rc) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&p->seq_exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            p->seq_exec = nullptr;
+            return fail(AC_ERR_CUDA, "sequential graph: %s", cudaGetErrorString(e));
+        }
+        p->seq_key[0] = u0;
+        p->seq_key[1] = b;
+        p->seq_key[2] = u;
+    }
+    CK(cudaGraphLaunch(p->seq_exec, st));
+    p->launches += p->seq_launches;
+    return AC_OK;
+}
+
 int ac_adjoint_solve(ac_plan* p, const double* g, double* lam, double tol, ac_stats* stats, void* stream) {
     if (!p || !g || !lam || g == lam) return fail(AC_ERR_INVALID_ARG, "bad argument");
     cudaStream_t st = (cudaStream_t)stream;
@@ -981,7 +1103,7 @@ int ac_grad_params(ac_plan* p, const double* u, const double* lam, double* du0, 
     a.u = u;
     a.lam = lam;
     a.dtQ = p->d_dtQ;
-    for (int i = 0; i < 5; ++i) {
+    for (int i = 0; i < 7; ++i) {
         a.d2x[i] = p->d2x[i];
         a.d1x[i] = p->d1x[i];
         a.d2y[i] = p->d2y[i];

@@ -7,7 +7,7 @@
 namespace ac {
 
 struct Nbr {
-    int dx[4], dy[4];  // offsets -1, +1, -2, +2 as deltas of the flat index
+    int dx[6], dy[6];  // offsets -1, +1, -2, +2, -3, +3 as deltas of the flat index
 };
 
 __device__ __forceinline__ Nbr neighbours(const Grid& g, long n) {
@@ -15,15 +15,14 @@ __device__ __forceinline__ Nbr neighbours(const Grid& g, long n) {
     const int nx = g.nx;
     const long iy = n / nx;
     const int ix = (int)(n - iy * nx);
-    const int offs[4] = {-1, 1, -2, 2};
 #pragma unroll
-    for (int o = 0; o < 4; ++o) {
-        int jx = ix + offs[o];
+    for (int o = 0; o < 6; ++o) {
+        int jx = ix + stencil_offset(o);
         jx = jx < 0 ? jx + nx : (jx >= nx ? jx - nx : jx);
         b.dx[o] = jx - ix;
         b.dy[o] = 0;
         if (g.dim == 2) {
-            long jy = iy + offs[o];
+            long jy = iy + stencil_offset(o);
             jy = jy < 0 ? jy + g.ny : (jy >= g.ny ? jy - g.ny : jy);
             b.dy[o] = (int)((jy - iy) * nx);
         }
@@ -31,16 +30,15 @@ __device__ __forceinline__ Nbr neighbours(const Grid& g, long n) {
     return b;
 }
 
-// sum_o tx[o] v(x+o) + ty[o] v(y+o) with the centre tap c
+// sum_o tx[o] v(x+o) + ty[o] v(y+o) with the centre tap c (taps on offsets -3..3)
 __device__ __forceinline__ double stencil(const double* v, const Nbr& b, int rad, int dim,
                                           const double* tx, const double* ty, double c) {
     double acc = c * v[0];
 #pragma unroll
-    for (int o = 0; o < 4; ++o) {
+    for (int o = 0; o < 6; ++o) {
         if (o < 2 * rad) {
-            const int tap = (o == 0) ? 1 : (o == 1) ? 3 : (o == 2) ? 0 : 4;
-            acc = fma(tx[tap], v[b.dx[o]], acc);
-            if (dim == 2) acc = fma(ty[tap], v[b.dy[o]], acc);
+            acc = fma(tx[stencil_tap(o)], v[b.dx[o]], acc);
+            if (dim == 2) acc = fma(ty[stencil_tap(o)], v[b.dy[o]], acc);
         }
     }
     return acc;
@@ -90,16 +88,13 @@ __global__ void __launch_bounds__(256) k_grad(GradArgs a) {
         const double* ub = a.u + (long)l * M * N + n;
         for (int j = 0; j < M; ++j) {
             const double* v = ub + (long)j * N;
-            Lu[j] = stencil(v, b, a.g.rad, a.g.dim, a.d2x, a.d2y, a.d2x[2] + (a.g.dim == 2 ? a.d2y[2] : 0.0));
-            Dx[j] = stencil(v, b, a.g.rad, 1, a.d1x, a.d1x, a.d1x[2]);
+            Lu[j] = stencil(v, b, a.g.rad, a.g.dim, a.d2x, a.d2y, a.d2x[3] + (a.g.dim == 2 ? a.d2y[3] : 0.0));
+            Dx[j] = stencil(v, b, a.g.rad, 1, a.d1x, a.d1x, a.d1x[3]);
             Dy[j] = 0.0;
             if (a.g.dim == 2) {
                 // y-derivative only: use the y offsets with the d1y taps
-                double acc = a.d1y[2] * v[0];
-                for (int o = 0; o < 2 * a.g.rad; ++o) {
-                    const int tap = (o == 0) ? 1 : (o == 1) ? 3 : (o == 2) ? 0 : 4;
-                    acc = fma(a.d1y[tap], v[b.dy[o]], acc);
-                }
+                double acc = a.d1y[3] * v[0];
+                for (int o = 0; o < 2 * a.g.rad; ++o) acc = fma(a.d1y[stencil_tap(o)], v[b.dy[o]], acc);
                 Dy[j] = acc;
             }
         }
@@ -304,5 +299,83 @@ cudaError_t launch_fill_stack(const double* u0, double* u, int L, int M, long lo
     k_fill_stack<<<grid, 256, 0, st>>>(u0, u, total, N);
     return cudaGetLastError();
 }
+
+// Sequential collocation stepping by diagonalisation of Q (the baseline the
+// paper calls T_Mpar, Sec. 4.2): with Q = S diag(lambda) S^{-1}, one step
+//   (I - dT Q (x) A) u_l = 1 (x) u_{l-1,M} + v_l
+// is z = (S^{-1} (x) I) rhs, M shifted solves (I - dT lambda_m A) z_m, and
+// u_l = (S (x) I) z.  k_seq_in forms z (transform precision), k_seq_out
+// forms u_l (real part, FP64).
+template <typename R>
+__global__ void __launch_bounds__(256) k_seq_in(int M, long N, const double* __restrict__ uprev,
+                                                const double* __restrict__ v, const double* __restrict__ Sinv,
+                                                typename Cx<R>::T* __restrict__ X) {
+    typedef typename Cx<R>::T C;
+    for (long n = blockIdx.x * (long)blockDim.x + threadIdx.x; n < N; n += (long)gridDim.x * blockDim.x) {
+        const double up = uprev[n];
+        double w[4];
+        for (int j = 0; j < M; ++j) w[j] = up + (v ? v[(long)j * N + n] : 0.0);
+        for (int m = 0; m < M; ++m) {
+            double re = 0.0, im = 0.0;
+            for (int j = 0; j < M; ++j) {
+                re = fma(Sinv[2 * (m * M + j)], w[j], re);
+                im = fma(Sinv[2 * (m * M + j) + 1], w[j], im);
+            }
+            C z;
+            z.x = (R)re;
+            z.y = (R)im;
+            X[(long)m * N + n] = z;
+        }
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_seq_out(int M, long N, const typename Cx<R>::T* __restrict__ X,
+                                                 const double* __restrict__ S, double* __restrict__ out) {
+    typedef typename Cx<R>::T C;
+    for (long n = blockIdx.x * (long)blockDim.x + threadIdx.x; n < N; n += (long)gridDim.x * blockDim.x) {
+        double zr[4], zi[4];
+        for (int j = 0; j < M; ++j) {
+            const C z = X[(long)j * N + n];
+            zr[j] = (double)z.x;
+            zi[j] = (double)z.y;
+        }
+        for (int m = 0; m < M; ++m) {
+            double acc = 0.0;
+            for (int j = 0; j < M; ++j) {
+                acc = fma(S[2 * (m * M + j)], zr[j], acc);
+                acc = fma(-S[2 * (m * M + j) + 1], zi[j], acc);
+            }
+            out[(long)m * N + n] = acc;
+        }
+    }
+}
+
+static int seq_grid(long long N) {
+    long g = (long)((N + 255) / 256);
+    return (int)(g > 152 * 8 ? 152 * 8 : g);
+}
+
+template <typename R>
+cudaError_t launch_seq_in(int M, long long N, const double* uprev, const double* v, const double* Sinv, void* X,
+                          cudaStream_t st) {
+    if (M < 1 || M > 4) return cudaErrorInvalidValue;
+    k_seq_in<R><<<seq_grid(N), 256, 0, st>>>(M, N, uprev, v, Sinv, reinterpret_cast<typename Cx<R>::T*>(X));
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_seq_out(int M, long long N, const void* X, const double* S, double* out, cudaStream_t st) {
+    if (M < 1 || M > 4) return cudaErrorInvalidValue;
+    k_seq_out<R><<<seq_grid(N), 256, 0, st>>>(M, N, reinterpret_cast<const typename Cx<R>::T*>(X), S, out);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_seq_in<float>(int, long long, const double*, const double*, const double*, void*,
+                                          cudaStream_t);
+template cudaError_t launch_seq_in<double>(int, long long, const double*, const double*, const double*, void*,
+                                           cudaStream_t);
+template cudaError_t launch_seq_out<float>(int, long long, const void*, const double*, double*, cudaStream_t);
+template cudaError_t launch_seq_out<double>(int, long long, const void*, const double*, double*, cudaStream_t);
 
 }  // namespace ac

@@ -5,12 +5,17 @@
 
 namespace ac {
 
+// Off-centre stencil offsets in the order the kernels visit them (radius 1,
+// then 2, then 3) and the matching tap index offset + 3.
+__host__ __device__ constexpr int stencil_offset(int o) { return (o & 1) ? (o >> 1) + 1 : -((o >> 1) + 1); }
+__host__ __device__ constexpr int stencil_tap(int o) { return stencil_offset(o) + 3; }
+
 // Geometry of the periodic grid and the per-axis stencil of A.
 struct Grid {
     int dim, nx, ny, N;      // N = nx * ny (ny = 1 in 1D)
-    int rad;                 // stencil radius (1 or 2)
-    double tx[5], ty[5];     // per-axis taps on offsets -2..2 (A = x part + y part)
-    double c0;               // tx[2] + ty[2], the combined centre tap
+    int rad;                 // stencil radius (1..3)
+    double tx[7], ty[7];     // per-axis taps on offsets -3..3 (A = x part + y part)
+    double c0;               // tx[3] + ty[3], the combined centre tap
 };
 
 // Residual + alpha-scaling + forward time FFT + node mixing (steps i-ii and
@@ -71,6 +76,15 @@ struct BicgArgs {
     int* iters;                  // [planes] iterations used (negative on breakdown)
 };
 
+struct GmresArgs {
+    Grid g;
+    int planes, M, max_iter, restart;
+    double tau;
+    void* X;                     // in: right-hand sides, out: solutions
+    const void* mu_dT;
+    int* iters;                  // [planes] Arnoldi steps used (encoding as BicgArgs)
+};
+
 struct ApplyArgs {
     Grid g;
     int M, L, transposed;
@@ -85,11 +99,22 @@ struct GradArgs {
     const double* u;
     const double* lam;
     const double* dtQ;           // [M][M] dT * Q
-    double d2x[5], d1x[5], d2y[5], d1y[5];  // second/first derivative taps per axis
+    double d2x[7], d1x[7], d2y[7], d1y[7];  // second/first derivative taps per axis, offsets -3..3
     double* part;                // [gridDim.x][3]
 };
 
 template <typename R> cudaError_t launch_fwd(const FwdArgs& a, int grid, size_t smem, cudaStream_t st);
+// sequential stepping by diagonalisation of Q: z = (S^{-1} (x) I)(1 (x) uprev + v)
+// (v: M*N or null; Sinv, S: M*M complex as interleaved doubles; X: M*N complex
+// of precision R), and out = Re (S (x) I) z
+template <typename R>
+cudaError_t launch_seq_in(int M, long long N, const double* uprev, const double* v, const double* Sinv, void* X,
+                          cudaStream_t st);
+template <typename R>
+cudaError_t launch_seq_out(int M, long long N, const void* X, const double* S, double* out, cudaStream_t st);
+template <typename R> cudaError_t launch_gmres(const GmresArgs& a, void* scratch, cudaStream_t st);
+// bytes of Krylov vectors per system (basis of restart + 1 vectors and x)
+size_t gmres_vector_bytes(int restart, long long N, size_t csize);
 template <typename R> cudaError_t launch_upd(const UpdArgs& a, int grid, size_t smem, cudaStream_t st);
 // shared memory the update kernel needs for these arguments (rsize = bytes per real of the transform)
 size_t upd_smem(const UpdArgs& a, size_t rsize);

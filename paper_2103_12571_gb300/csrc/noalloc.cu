@@ -154,9 +154,10 @@ int run(const ac_problem* prob, int M, int L, double dT, double alpha, const dou
     double t[8], Q[64];
     ac::radau_nodes(M, t);
     ac::collocation_matrix(M, t, Q);
-    double tx[5] = {0}, ty[5] = {0};
-    ac::axis_taps(prob->order, nx, prob->lx, prob->nu, prob->cx, tx);
-    if (prob->dim == 2) ac::axis_taps(prob->order, ny, prob->ly, prob->nu, prob->cy, ty);
+    ac::Stencil sten;
+    if (!ac::problem_stencil(*prob, &sten)) return nfail(AC_ERR_INVALID_ARG, "unsupported stencil");
+    const double* tx = sten.tx;
+    const double* ty = sten.ty;
     auto tw = [](int n) {
         std::vector<ac::cd> v(n);
         for (int k = 0; k < n; ++k) v[k] = std::exp(ac::cd(0.0, -2.0 * M_PI * k / n));
@@ -202,12 +203,12 @@ int run(const ac_problem* prob, int M, int L, double dT, double alpha, const dou
     g.nx = nx;
     g.ny = ny;
     g.N = (int)N;
-    g.rad = prob->order == 4 ? 2 : 1;
-    for (int i = 0; i < 5; ++i) {
+    g.rad = sten.rad;
+    for (int i = 0; i < 7; ++i) {
         g.tx[i] = tx[i];
         g.ty[i] = ty[i];
     }
-    g.c0 = tx[2] + ty[2];
+    g.c0 = tx[3] + ty[3];
 
     ac::FwdArgs fa{};
     fa.g = g;
@@ -279,7 +280,8 @@ extern "C" int ac_precond_solve_noalloc(const ac_problem* prob, int M, int L, do
                                         int precision, const double* r, double* e, void* stream) {
     if (!prob || !r || !e) return nfail(AC_ERR_INVALID_ARG, "null argument");
     if (prob->dim != 1 && prob->dim != 2) return nfail(AC_ERR_INVALID_ARG, "dim must be 1 or 2");
-    if (prob->order != 2 && prob->order != 4) return nfail(AC_ERR_INVALID_ARG, "order must be 2 or 4");
+    if (prob->upwind ? (prob->order < 1 || prob->order > 5) : (prob->order != 2 && prob->order != 4 && prob->order != 6))
+        return nfail(AC_ERR_INVALID_ARG, "order must be 2, 4 or 6 (centred) or 1..5 (upwind)");
     const int ny = prob->dim == 2 ? prob->ny : 1;
     if (prob->nx < 2 || (prob->dim == 2 && ny < 2) || !pow2(prob->nx) || !pow2(ny))
         return nfail(AC_ERR_INVALID_ARG, "grid sizes must be powers of two >= 2");

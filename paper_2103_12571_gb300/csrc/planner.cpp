@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 
 #include "alphacirc.h"
@@ -316,32 +317,96 @@ double freq_tables(int M, int L, double alpha, bool transposed, const double* Q,
 }
 
 // ---------------------------------------------------------------- stencils
-void central_coeffs(int order, double d1[5], double d2[5]) {
-    for (int i = 0; i < 5; ++i) d1[i] = d2[i] = 0.0;
-    if (order == 4) {
-        d1[0] = 1.0 / 12; d1[1] = -8.0 / 12; d1[3] = 8.0 / 12; d1[4] = -1.0 / 12;
-        d2[0] = -1.0 / 12; d2[1] = 16.0 / 12; d2[2] = -30.0 / 12; d2[3] = 16.0 / 12; d2[4] = -1.0 / 12;
-    } else {
-        d1[1] = -0.5; d1[3] = 0.5;
-        d2[1] = 1.0; d2[2] = -2.0; d2[3] = 1.0;
+// Standard finite-difference weights (exact on polynomials up to the degree
+// the number of points allows), as integer numerators over a denominator,
+// on consecutive offsets starting at lo.
+namespace {
+struct FdRow {
+    int lo, den, n;
+    int num[7];
+};
+// centred first derivative, order 2, 4, 6
+const FdRow kCentralD1[3] = {{-1, 2, 3, {-1, 0, 1}},
+                             {-2, 12, 5, {1, -8, 0, 8, -1}},
+                             {-3, 60, 7, {-1, 9, -45, 0, 45, -9, 1}}};
+// centred second derivative, order 2, 4, 6
+const FdRow kCentralD2[3] = {{-1, 1, 3, {1, -2, 1}},
+                             {-2, 12, 5, {-1, 16, -30, 16, -1}},
+                             {-3, 180, 7, {2, -27, 270, -490, 270, -27, 2}}};
+// upwind-biased first derivative for a positive velocity, order 1..5
+const FdRow kUpwindD1[5] = {{-1, 1, 2, {-1, 1}},
+                            {-2, 2, 3, {1, -4, 3}},
+                            {-2, 6, 4, {1, -6, 3, 2}},
+                            {-3, 12, 5, {-1, 6, -18, 10, 3}},
+                            {-3, 60, 6, {-2, 15, -60, 20, 30, -3}}};
+
+void put_row(const FdRow& r, double w[7], bool mirror) {
+    for (int i = 0; i < 7; ++i) w[i] = 0.0;
+    for (int j = 0; j < r.n; ++j) {
+        const int o = r.lo + j;
+        const double v = (double)r.num[j] / r.den;
+        if (mirror) w[3 - o] = -v;   // w'(o) = -w(-o)
+        else w[3 + o] = v;
     }
 }
 
-void axis_taps(int order, int n, double length, double nu, double c, double taps[5]) {
-    double d1[5], d2[5];
-    central_coeffs(order, d1, d2);
-    double h = length / n;
-    for (int i = 0; i < 5; ++i) taps[i] = nu * d2[i] / (h * h) - c * d1[i] / h;
+int support(const double w[7]) {
+    int r = 0;
+    for (int o = -3; o <= 3; ++o)
+        if (w[o + 3] != 0.0) r = std::max(r, std::abs(o));
+    return r;
+}
+}  // namespace
+
+bool derivative_weights(int order, int upwind, double c, double d1[7], double d2[7]) {
+    if (upwind) {
+        if (order < 1 || order > 5) return false;
+        put_row(kUpwindD1[order - 1], d1, c < 0.0);
+        const int lap = order + (order & 1);
+        put_row(kCentralD2[lap / 2 - 1], d2, false);
+    } else {
+        if (order != 2 && order != 4 && order != 6) return false;
+        put_row(kCentralD1[order / 2 - 1], d1, false);
+        put_row(kCentralD2[order / 2 - 1], d2, false);
+    }
+    return true;
 }
 
-void axis_symbol(int n, const double taps[5], cd* sigma) {
+bool problem_stencil(const ac_problem& prob, Stencil* st) {
+    const int dim = prob.dim;
+    double d1[7], d2[7];
+    int rad = 1;
+    for (int i = 0; i < 7; ++i) st->tx[i] = st->ty[i] = st->d1x[i] = st->d2x[i] = st->d1y[i] = st->d2y[i] = 0.0;
+    const double hx = prob.lx / prob.nx;
+    if (!derivative_weights(prob.order, prob.upwind, prob.cx, d1, d2)) return false;
+    rad = std::max(rad, std::max(support(d1), support(d2)));
+    for (int i = 0; i < 7; ++i) {
+        st->d1x[i] = d1[i] / hx;
+        st->d2x[i] = d2[i] / (hx * hx);
+        st->tx[i] = prob.nu * st->d2x[i] - prob.cx * st->d1x[i];
+    }
+    if (dim == 2) {
+        const double hy = prob.ly / prob.ny;
+        if (!derivative_weights(prob.order, prob.upwind, prob.cy, d1, d2)) return false;
+        rad = std::max(rad, std::max(support(d1), support(d2)));
+        for (int i = 0; i < 7; ++i) {
+            st->d1y[i] = d1[i] / hy;
+            st->d2y[i] = d2[i] / (hy * hy);
+            st->ty[i] = prob.nu * st->d2y[i] - prob.cy * st->d1y[i];
+        }
+    }
+    st->rad = rad;
+    return true;
+}
+
+void axis_symbol(int n, const double taps[7], cd* sigma) {
     for (int k = 0; k < n; ++k) {
         cd s = 0.0;
-        for (int o = -2; o <= 2; ++o) {
-            if (taps[o + 2] == 0.0) continue;
-            long long ko = ((long long)k * (o + n)) % n;  // k*o mod n, nonnegative
+        for (int o = -3; o <= 3; ++o) {
+            if (taps[o + 3] == 0.0) continue;
+            long long ko = (((long long)k * o) % n + n) % n;  // k*o mod n, nonnegative
             double th = 2.0 * M_PI * (double)ko / n;
-            s += taps[o + 2] * cd(std::cos(th), std::sin(th));
+            s += taps[o + 3] * cd(std::cos(th), std::sin(th));
         }
         sigma[k] = s;
     }
@@ -350,6 +415,21 @@ void axis_symbol(int n, const double taps[5], cd* sigma) {
 }  // namespace ac
 
 // ------------------------------------------------------------- C ABI (host)
+extern "C" int ac_stencil_taps(const ac_problem* prob, double* tx, double* ty, int* rad) {
+    if (!prob || !tx || !ty) return AC_ERR_INVALID_ARG;
+    if ((prob->dim != 1 && prob->dim != 2) || prob->nx < 1 || (prob->dim == 2 && prob->ny < 1) ||
+        !(prob->lx > 0) || (prob->dim == 2 && !(prob->ly > 0)))
+        return AC_ERR_INVALID_ARG;
+    ac::Stencil st;
+    if (!ac::problem_stencil(*prob, &st)) return AC_ERR_INVALID_ARG;
+    for (int i = 0; i < 7; ++i) {
+        tx[i] = st.tx[i];
+        ty[i] = st.ty[i];
+    }
+    if (rad) *rad = st.rad;
+    return AC_OK;
+}
+
 extern "C" int ac_radau_nodes(int M, double* t) {
     if (!t) return AC_ERR_INVALID_ARG;
     return ac::radau_nodes(M, t) ? AC_OK : AC_ERR_INVALID_ARG;

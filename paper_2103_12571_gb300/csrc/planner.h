@@ -5,6 +5,8 @@
 #include <complex>
 #include <vector>
 
+#include "alphacirc.h"
+
 namespace ac {
 
 typedef std::complex<double> cd;
@@ -25,14 +27,23 @@ double eig_small(int n, const cd* B, cd* mu, cd* S, cd* Sinv);
 double freq_tables(int M, int L, double alpha, bool transposed, const double* Q,
                    const double* t, cd* mu, cd* Sinv, cd* P, double* cond);
 
-// Central-difference coefficients on offsets -2..2 (index o + 2):
-// d1: first derivative times h, d2: second derivative times h^2.
-void central_coeffs(int order, double d1[5], double d2[5]);
+// Finite-difference weights on offsets -3..3 (index o + 3) of the scheme
+// (order, upwind) for a velocity component c: d1 = first derivative times h
+// (upwind-biased against the sign of c when upwind), d2 = centred second
+// derivative times h^2.  False if the scheme is not supported.
+bool derivative_weights(int order, int upwind, double c, double d1[7], double d2[7]);
 
-// Per-axis taps of A = nu Lap - c d/dx on offsets -2..2 (index o + 2).
-void axis_taps(int order, int n, double length, double nu, double c, double taps[5]);
+// The stencil of a problem on offsets -3..3: per-axis taps of
+// A = nu Lap - c . grad, the scaled derivative weights d1/h and d2/h^2 per
+// axis, and the radius (largest offset used by either derivative).
+struct Stencil {
+    double tx[7], ty[7];
+    double d1x[7], d2x[7], d1y[7], d2y[7];
+    int rad;
+};
+bool problem_stencil(const ac_problem& prob, Stencil* st);
 
-// Symbol sigma(k) = sum_o taps[o] exp(2 pi i k o / n), k = 0..n-1.
-void axis_symbol(int n, const double taps[5], cd* sigma);
+// Symbol sigma(k) = sum_o taps[o + 3] exp(2 pi i k o / n), k = 0..n-1.
+void axis_symbol(int n, const double taps[7], cd* sigma);
 
 }  // namespace ac

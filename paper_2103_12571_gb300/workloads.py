@@ -70,9 +70,9 @@ def random_phase_bumps_2d(nx, ny, kscale=8.0, seed=0):
     return (u / np.max(np.abs(u))).reshape(-1)
 
 
-def problem(dim, nx, ny=1, nu=0.0, cx=0.0, cy=0.0, order=2, M=3, L=4, T=1.0):
+def problem(dim, nx, ny=1, nu=0.0, cx=0.0, cy=0.0, order=2, M=3, L=4, T=1.0, upwind=False):
     return dict(dim=dim, nx=nx, ny=ny if dim == 2 else 1, lx=1.0, ly=1.0, nu=nu,
-                cx=cx, cy=cy, order=order, M=M, L=L, T=T)
+                cx=cx, cy=cy, order=order, M=M, L=L, T=T, upwind=bool(upwind))
 
 
 def config(i):

@@ -178,11 +178,13 @@ BICG = [
 ]
 
 
+@pytest.mark.parametrize("inner", ["bicgstab", "gmres"])
 @pytest.mark.parametrize("prob", BICG, ids=ids)
 @pytest.mark.parametrize("precision", ["c128", "c64"])
-def test_precond_solve_bicgstab(prob, precision):
-    """Inexact inner solves: the preconditioner error is bounded by a
-    multiple of L (3 eps + tau) / alpha (Theorem 2)."""
+def test_precond_solve_krylov(prob, precision, inner):
+    """Inexact inner solves (BiCGStab, or GMRES as in the paper): the
+    preconditioner error is bounded by a multiple of L (3 eps + tau) / alpha
+    (Theorem 2)."""
     torch = torch_cuda()
     from paper_2103_12571_gb300.api import Plan
     Q, A, dT = oracle_setup(prob)
@@ -190,7 +192,7 @@ def test_precond_solve_bicgstab(prob, precision):
     r = rand_field(rng, prob)
     eps = EPS64 if precision == "c128" else EPS32
     tau = 1e-12 if precision == "c128" else 1e-6
-    plan = Plan(prob, precision=precision, inner="bicgstab", tau=tau)
+    plan = Plan(prob, precision=precision, inner=inner, tau=tau)
     alpha = 1e-2
     e = plan.precond_solve(alpha, to_dev(torch, r)).cpu().numpy()
     ref = paradiag.precond_solve(A, Q, dT, alpha, r).real
@@ -198,9 +200,10 @@ def test_precond_solve_bicgstab(prob, precision):
     assert rel2(e, ref) < tol, (rel2(e, ref), tol)
 
 
+@pytest.mark.parametrize("inner", ["bicgstab", "gmres"])
 @pytest.mark.parametrize("prob", BICG[:3], ids=ids)
 @pytest.mark.parametrize("precision,alpha_mode,tol,tau", [("c128", "paper", 1e-11, 1e-10), ("c64", "mixed", 1e-10, 1e-6)])
-def test_richardson_solve_bicgstab(prob, precision, alpha_mode, tol, tau):
+def test_richardson_solve_krylov(prob, precision, alpha_mode, tol, tau, inner):
     torch = torch_cuda()
     from paper_2103_12571_gb300.api import Plan
     Q, A, dT = oracle_setup(prob)
@@ -208,13 +211,36 @@ def test_richardson_solve_bicgstab(prob, precision, alpha_mode, tol, tau):
     N = operators.n_points(prob)
     u0 = rng.standard_normal(N)
     ref = sequential.sequential_solve(A, Q, dT, prob["L"], u0)
-    plan = Plan(prob, precision=precision, inner="bicgstab", tau=tau, alpha=alpha_mode, max_iter=60)
+    plan = Plan(prob, precision=precision, inner=inner, tau=tau, alpha=alpha_mode, max_iter=60)
     u, st = plan.solve(to_dev(torch, u0), tol=1e-13, raise_on_fail=False)
     err = rel2(u.cpu().numpy(), ref)
     assert err < tol, (err, st)
     assert all(v > 0 for v in st["inner_iters"]), st
     if precision == "c128":   # in complex64, systems stagnating at the FP32 floor are expected
         assert not any(st["inner_failed"]), st
+
+
+@pytest.mark.parametrize("restart", [1, 4, 32])
+def test_gmres_restart_lengths(restart):
+    """GMRES(m) for m = 1 (a minimal-residual iteration), 4 and 32 (the
+    largest): the preconditioner solve meets the Theorem 2 bound and the
+    reported inner iteration counts are consistent with the restart length."""
+    torch = torch_cuda()
+    from paper_2103_12571_gb300.api import Plan
+    prob = workloads.problem(2, 24, 20, nu=0.02, cx=0.4, cy=-0.3, order=4, M=3, L=8, T=0.05)
+    Q, A, dT = oracle_setup(prob)
+    r = rand_field(np.random.default_rng(14), prob)
+    plan = Plan(prob, precision="c128", inner="gmres", tau=1e-12, inner_restart=restart)
+    alpha = 1e-2
+    e = plan.precond_solve(alpha, to_dev(torch, r)).cpu().numpy()
+    ref = paradiag.precond_solve(A, Q, dT, alpha, r).real
+    assert rel2(e, ref) < 20 * prob["L"] * (3 * EPS64 + 1e-12) / alpha
+    u0 = np.random.default_rng(15).standard_normal(480)
+    plan2 = Plan(prob, precision="c128", inner="gmres", tau=1e-12, inner_restart=restart, alpha="paper", max_iter=30)
+    u, st = plan2.solve(to_dev(torch, u0), tol=1e-13, raise_on_fail=False)
+    assert rel2(u.cpu().numpy(), sequential.sequential_solve(A, Q, dT, 8, u0)) < 1e-11, st
+    assert not any(st["inner_failed"]), st
+    assert all(v > 0 for v in st["inner_iters"]), st
 
 
 def test_unaligned_buffers_take_the_scalar_path():

@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 from conftest import ROOT
-from oracle import alpha_rule, collocation, paradiag
+from oracle import alpha_rule, collocation, paradiag, stencils
 
 
 @pytest.fixture(scope="module")
@@ -101,3 +101,43 @@ def test_setup_rejects_bad_arguments(api):
         assert e.value.code == -1
     with pytest.raises(ACError):
         api.Plan(workloads.problem(1, 48, nu=0.1, M=2, L=4), inner="fft")
+
+
+SCHEMES = [(p, False) for p in (2, 4, 6)] + [(p, True) for p in (1, 2, 3, 4, 5)]
+
+
+@pytest.mark.parametrize("order,upwind", SCHEMES)
+def test_host_stencil_taps_match_oracle(api, order, upwind):
+    """ac_stencil_taps against the oracle's finite-difference weights (derived
+    there from the moment conditions), both signs of each velocity, 1D and
+    2D, non-unit box lengths."""
+    from paper_2103_12571_gb300 import workloads
+    for dim, cx, cy in ((1, 0.7, 0.0), (1, -1.3, 0.0), (2, -0.4, 0.9), (2, 1.1, -0.2)):
+        prob = workloads.problem(dim, 48, 40, nu=0.03, cx=cx, cy=cy, order=order, upwind=upwind)
+        prob["lx"], prob["ly"] = 2.0, 0.5
+        tx, ty, rad = api.stencil_taps(prob)
+        want = {}
+        for axis, n, length, c in (("x", 48, 2.0, cx), ("y", 40, 0.5, cy)):
+            h = length / n
+            w = np.zeros(7)
+            if axis == "x" or dim == 2:
+                for o, v in stencils.d2_weights(order, upwind).items():
+                    w[o + 3] += 0.03 * float(v) / h ** 2
+                for o, v in stencils.d1_weights(order, upwind, c).items():
+                    w[o + 3] -= c * float(v) / h
+            want[axis] = w
+        np.testing.assert_allclose(tx, want["x"], rtol=1e-14, atol=1e-12)
+        np.testing.assert_allclose(ty, want["y"], rtol=1e-14, atol=1e-12)
+        sup = max(abs(o) for o in list(stencils.d1_weights(order, upwind, 1.0)) +
+                  list(stencils.d2_weights(order, upwind)))
+        assert rad == sup
+
+
+def test_host_stencil_taps_reject_unsupported(api):
+    from paper_2103_12571_gb300 import workloads
+    from paper_2103_12571_gb300._lib import ACError
+    for order, upwind in ((3, False), (8, False), (0, True), (6, True)):
+        with pytest.raises(ACError):
+            api.stencil_taps(workloads.problem(1, 32, nu=0.1, cx=1.0, order=order, upwind=upwind))
+        with pytest.raises(ACError):
+            api.Plan(workloads.problem(1, 32, nu=0.1, cx=1.0, order=order, upwind=upwind, M=2, L=4))
