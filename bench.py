@@ -8,8 +8,11 @@ periodic heat test shape with synthetic data.  One step = one Richardson
 iteration u <- u + C_alpha^{-1}(w - C u) of the mixed form (FP64 residual and
 update, complex64 preconditioner) with the mixed-rule alpha.
 
-Prints one JSON line (rank 0).  --impl reference times the CPU oracle
-instead.
+Prints one JSON line (rank 0).  Beside the headline it carries the
+end-to-end figure, the time to a 1e-10 residual in FP64 and mixed precision,
+the sequential baseline on the same GPU, per-step times and solves of all
+five workloads, and the roofline of the dominant kernel.  --impl reference
+times the CPU oracle instead.
 """
 import argparse
 import json
@@ -265,6 +268,32 @@ def run_ours(args):
             ttt[name]["kernel_ms"] = {k: round(v[0], 4) for k, v in p2.profile_read().items() if v[1]}
             del p2
 
+    # ---- the sequential baseline of Sec. 4.2 on the same GPU: the L steps one
+    # after another, each by diagonalisation of Q (FP64, replayed from a CUDA
+    # graph), and the speedup of the all-at-once solves to 1e-10 over it
+    pseq = Plan(prob, precision="c128")
+    useq = pseq.sequential_solve(u0)          # capture the graph, warm
+    umix, _ = plan.solve(u0, TOL)
+    seq_runs = []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        pseq.sequential_solve(u0, out=useq)
+        b.record(st)
+        torch.cuda.synchronize()
+        seq_runs.append(a.elapsed_time(b))
+    seq_ms = float(np.median(seq_runs))
+    seq = {"ms": round(seq_ms, 3), "what": "L sequential Radau IIA steps by diagonalisation of Q, FP64, one GPU",
+           "speedup_fp64": round(seq_ms / ttt["fp64"]["ms"], 3),
+           "speedup_mixed": round(seq_ms / ttt["mixed"]["ms"], 3),
+           "rel_diff_mixed_vs_sequential": float("%.3e" % float(torch.linalg.norm(umix - useq) /
+                                                                  torch.linalg.norm(useq)))}
+    del pseq
+
+    configs = all_configs(torch, st, flush) if not args.no_configs else None
+
     # ---- roofline of the dominant kernel
     kern = {k: v for k, v in prof.items() if v[1] > 0}
     dom = max(kern, key=lambda k: kern[k][0])
@@ -283,6 +312,8 @@ def run_ours(args):
         "gpu_launches": int(launches),
         "kernels_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in kern.items()},
         "time_to_1e-10": ttt,
+        "sequential_baseline": seq,
+        "all_configs": configs,
         "roofline": roof,
         "clocks": clk,
         "wall_s_timed": wall,
@@ -293,6 +324,83 @@ def run_ours(args):
         print(json.dumps(out))
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def _timed(torch, st, fn, reps=1, flush=None):
+    """Median device time (ms) of fn() over reps runs, CUDA events on st."""
+    out = []
+    for _ in range(reps):
+        if flush is not None:
+            flush_l2(torch, flush)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        fn()
+        b.record(st)
+        torch.cuda.synchronize()
+        out.append(a.elapsed_time(b))
+    return float(np.median(out))
+
+
+def all_configs(torch, st, flush):
+    """The five workloads: one Richardson step in each precision (DoF*it/s),
+    and their solves (iterations and time to tolerance)."""
+    from paper_2103_12571_gb300 import workloads
+    from paper_2103_12571_gb300.api import Plan
+    res = {}
+    for i in range(1, 6):
+        prob, u0n, ex = workloads.config(i)
+        L, M = prob["L"], prob["M"]
+        N = prob["nx"] * prob["ny"]
+        D = L * M * N
+        u0 = torch.from_numpy(u0n).cuda()
+        r = {"DoF": D, "step_ms": {}, "dof_it_per_s": {}, "solve": {}}
+        for prec in ("c64", "c128"):
+            plan = Plan(prob, precision=prec, alpha="mixed")
+            eps = 2.0 ** -24 if prec == "c64" else 2.0 ** -53
+            a = min(0.25, max(1e-8, (L * 3 * eps) ** 0.5))      # the mixed-rule alpha
+            u = u0.repeat(L * M).reshape(L, M, N).contiguous()
+            for _ in range(3):
+                plan.richardson_step(a, u0, u)
+            ms = _timed(torch, st, lambda: plan.richardson_step(a, u0, u), reps=5, flush=flush)
+            r["step_ms"][prec] = round(ms, 4)
+            r["dof_it_per_s"][prec] = D / (ms * 1e-3)
+            del plan, u
+        # solves as each workload is specified
+        runs = []
+        if i == 1:
+            runs.append(("fp64_fixed_alpha", dict(precision="c128", alpha="fixed", alpha0=ex["alpha"]), ex["tol"]))
+        else:
+            runs.append(("fp64", dict(precision="c128", alpha="paper"), TOL))
+            runs.append(("mixed", dict(precision="c64", alpha="mixed"), TOL))
+        for name, kw, tol in runs:
+            plan = Plan(prob, max_iter=60, **kw)
+            plan.solve(u0, tol)                      # warm (tables, allocations)
+            box = {}
+
+            def go():
+                box["u"], box["st"] = plan.solve(u0, tol)
+            ms = _timed(torch, st, go)
+            r["solve"][name] = {"ms": round(ms, 3), "iters": box["st"]["iters"], "tol": tol,
+                                "res_rel": float("%.3e" % box["st"]["res_rel"][-1])}
+            del plan, box
+        if i == 4:
+            # forward + adjoint + gradients (FP64), the workload's training step
+            plan = Plan(prob, precision="c128", alpha="paper", max_iter=60)
+            target = torch.from_numpy(ex["u_target"]).cuda()
+
+            def fwd_bwd():
+                u, _ = plan.solve(u0, 1e-13, raise_on_fail=False)
+                g = torch.zeros_like(u)
+                g[-1, -1] = 2.0 * (u[-1, -1] - target)
+                lam, _ = plan.adjoint_solve(g, 1e-13, raise_on_fail=False)
+                plan.grad_params(u, lam)
+            fwd_bwd()
+            r["forward_adjoint_grad_ms"] = round(_timed(torch, st, fwd_bwd), 3)
+            del plan
+        res[ex["name"]] = r
+        torch.cuda.empty_cache()
+    return res
 
 
 def cpu_baseline(prob, u0, samples=1):
@@ -388,6 +496,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-samples", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-configs", action="store_true", help="skip the per-workload section")
     ap.add_argument("--no-extras", action="store_true",
                     help="only the timed steps (used for ncu captures): no e2e, time-to-tolerance or CPU legs")
     args = ap.parse_args()

@@ -221,6 +221,23 @@ int ac_window_solve(ac_plan* plan, const double* u0, int n_windows, double* u_en
  * per-system status is not reported here.  Not thread-safe per plan. */
 int ac_sequential_solve(ac_plan* plan, const double* u0, const double* b, double* u, void* stream);
 
+/* Outer Krylov acceleration (the coupling the paper names as future work in
+ * Sec. 6): flexible GMRES(m) on C u = w, right-preconditioned by C_alpha^{-1}
+ * (the same preconditioner kernels as the Richardson iteration), FP64
+ * vectors, classical Gram-Schmidt with one reorthogonalisation, restarted
+ * every m = restart steps (<= 0: 10; at most 32) with the true residual
+ * recomputed at each restart.  alpha: the plan's fixed alpha0 for
+ * AC_ALPHA_FIXED, else the correction-form rule sqrt(L (3 eps + tau)).
+ * Stops when ||w - C u||_2 <= tol ||w||_2 (true residual at a restart), or
+ * after the plan's max_iter preconditioned steps (AC_ERR_NO_CONVERGENCE; u
+ * holds the last iterate).  u0, b, u as in ac_richardson_solve (u0 may be
+ * NULL only with init_u = 1 and b given).  stats: iters = preconditioned
+ * steps; res_rel[k] = GMRES residual estimate after step k, replaced by the
+ * true residual at each restart; alpha[k] = alpha.  Workspace: 2m + 2
+ * space-time vectors, allocated on first use and kept by the plan. */
+int ac_krylov_solve(ac_plan* plan, const double* u0, const double* b, double* u, int init_u, double tol,
+                    int restart, ac_stats* stats, void* stream);
+
 /* ---- adjoint (not in the paper; derived from eq. (globalsys)) ----------- */
 
 /* lam = C^{-T} g.  Reversing the time index turns C^T into a system of the

@@ -73,6 +73,7 @@ _PROTOS = {
     "ac_grad_params": (_I, [_P, _P, _P, _P, _P, _P]),
     "ac_precond_solve_noalloc": (_I, [ctypes.POINTER(Problem), _I, _I, _D, _D, _I, _P, _P, _P]),
     "ac_sequential_solve": (_I, [_P, _P, _P, _P, _P]),
+    "ac_krylov_solve": (_I, [_P, _P, _P, _P, _I, _D, _I, _P, _P]),
     "ac_radau_nodes": (_I, [_I, _P]),
     "ac_stencil_taps": (_I, [ctypes.POINTER(Problem), _P, _P, _P]),
     "ac_collocation_matrix": (_I, [_I, _P]),

@@ -141,6 +141,18 @@ class Plan:
                                         ctypes.byref(st), ctypes.byref(tot), _stream()), "ac_window_solve")
         return u_end, tot.value, stats_dict(st)
 
+    def krylov_solve(self, u0, tol, b=None, u=None, restart=10, raise_on_fail=True):
+        """Outer flexible GMRES(restart) on C u = w, right-preconditioned by
+        C_alpha^{-1}; returns (u, stats)."""
+        init = u is not None
+        u = self.empty() if u is None else u
+        st = C.Stats()
+        rc = C.lib().ac_krylov_solve(self._h, _ptr(u0), _ptr(b), _ptr(u), int(init), float(tol), int(restart),
+                                     ctypes.byref(st), _stream())
+        if rc != C.AC_OK and (raise_on_fail or rc != C.AC_ERR_NO_CONVERGENCE):
+            C.check(rc, "ac_krylov_solve")
+        return u, stats_dict(st)
+
     def sequential_solve(self, u0, b=None, out=None):
         """The L steps one after another by diagonalisation of Q (the
         paper's sequential baseline), replayed from a CUDA graph."""

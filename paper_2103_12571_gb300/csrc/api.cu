@@ -116,6 +116,11 @@ struct ac_plan {
     cudaGraphExec_t seq_exec = nullptr;
     const void* seq_key[3] = {nullptr, nullptr, nullptr};
     long long seq_launches = 0;     // kernels per replay of the graph
+    // outer flexible GMRES (ac_krylov_solve)
+    double* d_kry = nullptr;        // 2m + 2 space-time vectors
+    int kry_m = 0;
+    double* d_kpart = nullptr;      // [8][krylov_grid] partial dot products
+    double* h_kpart = nullptr;      // pinned copy
     // profiling
     bool prof = false;
     std::vector<EventPair> pending;
@@ -275,6 +280,12 @@ static int run_spatial(ac_plan* p, void* X, const void* mu_dT, int planes, int t
     sa.tw_y = p->tw_y;
     sa.rows_per_block = p->rows_per_block;
     sa.cols_per_block = p->cols_per_block;
+    if (p->spatial_path == 2) {
+        // few planes (sequential stepping): smaller tiles, so that each pass
+        // still has two CTAs per SM
+        while (sa.rows_per_block > 1 && (long)planes * sa.ny / sa.rows_per_block < 2 * 152) sa.rows_per_block >>= 1;
+        while (sa.cols_per_block > 2 && (long)planes * sa.nx / sa.cols_per_block < 2 * 152) sa.cols_per_block >>= 1;
+    }
     if (p->spatial_path == 0) {
         CK(ac::launch_space_1d<R>(sa, st));
         p->launches++;
@@ -679,6 +690,62 @@ static int seq_steps(ac_plan* p, const double* u0, const double* b, double* u, c
     return AC_OK;
 }
 
+// ------------------------------------------------ outer Krylov (FGMRES)
+// dot products out[j] = <V_j, w>, j < k (8 per pass over w; host sums the
+// per-block partials)
+static int kry_dots(ac_plan* p, double* const* V, int k, const double* w, double* out, cudaStream_t st) {
+    const int G = ac::krylov_grid();
+    const long long n = (long long)p->L * p->M * p->N;
+    for (int j0 = 0; j0 < k; j0 += 8) {
+        const int kk = std::min(8, k - j0);
+        ac::VecList vl{};
+        for (int j = 0; j < kk; ++j) vl.v[j] = V[j0 + j];
+        CK(ac::launch_mdot(vl, kk, w, n, p->d_kpart, st));
+        p->launches++;
+        CK(cudaMemcpyAsync(p->h_kpart, p->d_kpart, sizeof(double) * kk * G, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        for (int j = 0; j < kk; ++j) {
+            double sum = 0.0;
+            for (int b = 0; b < G; ++b) sum += p->h_kpart[(size_t)j * G + b];
+            out[j0 + j] = sum;
+        }
+    }
+    return AC_OK;
+}
+
+// y = beta y + sum_{j<k} c_j V_j
+static int kry_axpy(ac_plan* p, double* const* V, const double* c, int k, double beta, double* y, cudaStream_t st) {
+    const long long n = (long long)p->L * p->M * p->N;
+    int j0 = 0;
+    do {
+        const int kk = std::min(8, k - j0);
+        ac::VecList vl{};
+        ac::Coefs cf{};
+        for (int j = 0; j < kk; ++j) {
+            vl.v[j] = V[j0 + j];
+            cf.c[j] = c[j0 + j];
+        }
+        CK(ac::launch_maxpy(vl, cf, kk, j0 == 0 ? beta : 1.0, y, n, st));
+        p->launches++;
+        j0 += 8;
+    } while (j0 < k);
+    return AC_OK;
+}
+
+static int kry_alloc(ac_plan* p, int m) {
+    const size_t D = (size_t)p->L * p->M * p->N;
+    if (p->d_kry && p->kry_m >= m) return AC_OK;
+    if (p->d_kry) cudaFree(p->d_kry);
+    p->d_kry = nullptr;
+    p->kry_m = 0;
+    cudaError_t e = cudaMalloc((void**)&p->d_kry, sizeof(double) * D * (2 * (size_t)m + 2));
+    if (e == cudaSuccess && !p->d_kpart) e = cudaMalloc((void**)&p->d_kpart, sizeof(double) * 8 * ac::krylov_grid());
+    if (e == cudaSuccess && !p->h_kpart) e = cudaMallocHost((void**)&p->h_kpart, sizeof(double) * 8 * ac::krylov_grid());
+    if (e != cudaSuccess) return fail(AC_ERR_CUDA, "Krylov workspace: %s", cudaGetErrorString(e));
+    p->kry_m = m;
+    return AC_OK;
+}
+
 extern "C" {
 
 const char* ac_status_string(int s) {
@@ -713,8 +780,9 @@ void ac_destroy(ac_plan* p) {
     if (p->ev_res) cudaEventDestroy(p->ev_res);
     if (p->seq_exec) cudaGraphExecDestroy(p->seq_exec);
     if (p->seq_capture) cudaStreamDestroy(p->seq_capture);
-    for (void* b : {(void*)p->d_seq_S, (void*)p->d_seq_Sinv, p->d_seq_mu})
+    for (void* b : {(void*)p->d_seq_S, (void*)p->d_seq_Sinv, p->d_seq_mu, (void*)p->d_kry, (void*)p->d_kpart})
         if (b) cudaFree(b);
+    if (p->h_kpart) cudaFreeHost(p->h_kpart);
     delete p;
 }
 
@@ -1075,6 +1143,134 @@ int ac_sequential_solve(ac_plan* p, const double* u0, const double* b, double* u
     CK(cudaGraphLaunch(p->seq_exec, st));
     p->launches += p->seq_launches;
     return AC_OK;
+}
+
+int ac_krylov_solve(ac_plan* p, const double* u0, const double* b, double* u, int init_u, double tol, int restart,
+                    ac_stats* stats, void* stream) {
+    if (!p || !u || (!u0 && !b) || (!init_u && !u0)) return fail(AC_ERR_INVALID_ARG, "bad argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int m = restart > 0 ? std::min(restart, 32) : 10;
+    int rc = kry_alloc(p, m);
+    if (rc) return rc;
+    ac_stats local;
+    ac_stats* S = stats ? stats : &local;
+    std::memset(S, 0, sizeof(ac_stats));
+    double wn2 = 0, winf = 0;
+    rc = w_norms(p, u0, b, &wn2, &winf, st);
+    if (rc) return rc;
+    S->w_norm2 = wn2;
+    S->w_inf = winf;
+    if (!std::isfinite(wn2)) return fail(AC_ERR_NOT_FINITE, "right-hand side is not finite");
+    const size_t D = (size_t)p->L * p->M * p->N;
+    if (wn2 == 0.0) {
+        CK(cudaMemsetAsync(u, 0, sizeof(double) * D, st));
+        S->converged = 1;
+        return AC_OK;
+    }
+    // the preconditioner's alpha: the fixed one, else the correction-form rule
+    const double eps = p->precision == AC_C128 ? std::ldexp(1.0, -53) : std::ldexp(1.0, -24);
+    const double tau = p->inner != AC_INNER_FFT ? inner_tau(p) : 0.0;
+    const double alpha = p->sched.mode == AC_ALPHA_FIXED
+                             ? p->sched.alpha0
+                             : std::min(0.25, std::max(1e-8, std::sqrt(p->L * (3.0 * eps + tau))));
+    rc = ensure_tables(p, alpha, 0, pow2_scale(winf), st);
+    if (rc) return rc;
+    if (!init_u) {
+        CK(ac::launch_fill_stack(u0, u, p->L, p->M, p->N, st));
+        p->launches++;
+    }
+    std::vector<double*> V(m + 1), Z(m);
+    for (int i = 0; i <= m; ++i) V[i] = p->d_kry + (size_t)i * D;
+    for (int i = 0; i < m; ++i) Z[i] = p->d_kry + (size_t)(m + 1 + i) * D;
+    double* T = p->d_kry + (size_t)(2 * m + 1) * D;
+    const int max_steps = std::min(std::max(p->sched.max_iter, 1), AC_MAX_STATS - 1);
+    std::vector<double> H((size_t)(m + 1) * m), g(m + 1), cs(m), sn(m), h(m + 1), h2(m + 1), y(m);
+    int steps = 0;
+    bool converged = false;
+    for (;;) {
+        // true residual r = w - C u into V_0
+        rc = apply_impl(p, u, T, 0, st);
+        if (rc) return rc;
+        CK(ac::launch_w_minus(u0, b, T, V[0], p->L, p->M, p->N, st));
+        p->launches++;
+        double beta2 = 0.0;
+        rc = kry_dots(p, &V[0], 1, V[0], &beta2, st);
+        if (rc) return rc;
+        const double beta = std::sqrt(beta2);
+        S->res_rel[steps] = beta / wn2;
+        if (!std::isfinite(beta)) return fail(AC_ERR_NOT_FINITE, "residual is not finite");
+        if (beta <= tol * wn2) {
+            converged = true;
+            break;
+        }
+        if (steps >= max_steps) break;
+        const double ib = 1.0 / beta;
+        rc = kry_axpy(p, V.data(), nullptr, 0, ib, V[0], st);
+        if (rc) return rc;
+        std::fill(g.begin(), g.end(), 0.0);
+        g[0] = beta;
+        int j = 0;
+        for (; j < m; ++j) {
+            // z_j = C_alpha^{-1} v_j, w = C z_j (flexible: z_j kept)
+            rc = precond(p, nullptr, nullptr, V[j], 0, 0, Z[j], 0, st, false);
+            if (rc) return rc;
+            rc = apply_impl(p, Z[j], V[j + 1], 0, st);
+            if (rc) return rc;
+            // classical Gram-Schmidt, two passes
+            for (int i = 0; i <= j; ++i) H[(size_t)j * (m + 1) + i] = 0.0;
+            for (int pass = 0; pass < 2; ++pass) {
+                rc = kry_dots(p, V.data(), j + 1, V[j + 1], h.data(), st);
+                if (rc) return rc;
+                for (int i = 0; i <= j; ++i) {
+                    H[(size_t)j * (m + 1) + i] += h[i];
+                    h2[i] = -h[i];
+                }
+                rc = kry_axpy(p, V.data(), h2.data(), j + 1, 1.0, V[j + 1], st);
+                if (rc) return rc;
+            }
+            double hn2 = 0.0;
+            rc = kry_dots(p, &V[j + 1], 1, V[j + 1], &hn2, st);
+            if (rc) return rc;
+            const double hn = std::sqrt(hn2);
+            if (hn > 0.0) {
+                rc = kry_axpy(p, V.data(), nullptr, 0, 1.0 / hn, V[j + 1], st);
+                if (rc) return rc;
+            }
+            // Givens rotations on column j
+            double* hc = &H[(size_t)j * (m + 1)];
+            for (int i = 0; i < j; ++i) {
+                const double a0 = hc[i], a1 = hc[i + 1];
+                hc[i] = cs[i] * a0 + sn[i] * a1;
+                hc[i + 1] = -sn[i] * a0 + cs[i] * a1;
+            }
+            const double rho = std::hypot(hc[j], hn);
+            if (!(rho > 0.0)) return fail(AC_ERR_INNER_BREAKDOWN, "GMRES breakdown (singular Hessenberg)");
+            cs[j] = hc[j] / rho;
+            sn[j] = hn / rho;
+            hc[j] = rho;
+            g[j + 1] = -sn[j] * g[j];
+            g[j] = cs[j] * g[j];
+            S->alpha[steps] = alpha;
+            ++steps;
+            S->res_rel[steps] = std::fabs(g[j + 1]) / wn2;
+            if (std::fabs(g[j + 1]) <= tol * wn2 || hn == 0.0 || steps >= max_steps) {
+                ++j;
+                break;
+            }
+        }
+        const int k = std::min(j, m);
+        for (int i = k - 1; i >= 0; --i) {   // y = R^{-1} g
+            double acc = g[i];
+            for (int q = i + 1; q < k; ++q) acc -= H[(size_t)q * (m + 1) + i] * y[q];
+            y[i] = acc / H[(size_t)i * (m + 1) + i];
+        }
+        rc = kry_axpy(p, Z.data(), y.data(), k, 1.0, u, st);
+        if (rc) return rc;
+    }
+    S->iters = steps;
+    S->converged = converged ? 1 : 0;
+    return converged ? AC_OK : fail(AC_ERR_NO_CONVERGENCE, "outer GMRES: %d steps, residual %.3e", steps,
+                                    S->res_rel[steps]);
 }
 
 int ac_adjoint_solve(ac_plan* p, const double* g, double* lam, double tol, ac_stats* stats, void* stream) {

@@ -378,4 +378,76 @@ template cudaError_t launch_seq_in<double>(int, long long, const double*, const 
 template cudaError_t launch_seq_out<float>(int, long long, const void*, const double*, double*, cudaStream_t);
 template cudaError_t launch_seq_out<double>(int, long long, const void*, const double*, double*, cudaStream_t);
 
+// ---------------------------------------------- outer Krylov vector kernels
+// Space-time vectors of n FP64 values.  k_mdot: partial sums of <V_j, w>,
+// j < k <= 8 per launch (one pass over w), per block into part[j * grid + b].
+// k_maxpy: y = beta y + sum_j c_j V_j, j < k <= 8.
+__global__ void __launch_bounds__(256) k_mdot(VecList V, int k, const double* __restrict__ w, long n,
+                                              double* __restrict__ part) {
+    __shared__ double red[8 * 8];
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const double wi = w[i];
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            if (j < k) acc[j] = fma(V.v[j][i], wi, acc[j]);
+    }
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        double s = acc[j];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) red[j * 8 + wp] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < k) {
+        double s = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s += red[threadIdx.x * 8 + q];
+        part[(long)threadIdx.x * gridDim.x + blockIdx.x] = s;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_maxpy(VecList V, Coefs c, int k, double beta, double* __restrict__ y,
+                                               long n) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        double acc = beta == 0.0 ? 0.0 : beta * y[i];
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            if (j < k) acc = fma(c.c[j], V.v[j][i], acc);
+        y[i] = acc;
+    }
+}
+
+int krylov_grid() { return 152 * 8; }
+
+cudaError_t launch_mdot(const VecList& V, int k, const double* w, long long n, double* part, cudaStream_t st) {
+    if (k < 1 || k > 8) return cudaErrorInvalidValue;
+    k_mdot<<<krylov_grid(), 256, 0, st>>>(V, k, w, n, part);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_maxpy(const VecList& V, const Coefs& c, int k, double beta, double* y, long long n,
+                         cudaStream_t st) {
+    if (k < 0 || k > 8) return cudaErrorInvalidValue;
+    k_maxpy<<<krylov_grid(), 256, 0, st>>>(V, c, k, beta, y, n);
+    return cudaGetLastError();
+}
+
+// r = w - Cu with w = (u0 stacked in block 0) + b, natural time order
+__global__ void __launch_bounds__(256) k_w_minus(const double* __restrict__ u0, const double* __restrict__ b,
+                                                 const double* __restrict__ Cu, double* __restrict__ r, long MN,
+                                                 long N, long total) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
+        double w = (i < MN && u0) ? u0[i % N] : 0.0;
+        if (b) w += b[i];
+        r[i] = w - Cu[i];
+    }
+}
+
+cudaError_t launch_w_minus(const double* u0, const double* b, const double* Cu, double* r, int L, int M,
+                           long long N, cudaStream_t st) {
+    k_w_minus<<<krylov_grid(), 256, 0, st>>>(u0, b, Cu, r, (long)M * N, N, (long)L * M * N);
+    return cudaGetLastError();
+}
+
 }  // namespace ac

@@ -112,6 +112,22 @@ cudaError_t launch_seq_in(int M, long long N, const double* uprev, const double*
                           cudaStream_t st);
 template <typename R>
 cudaError_t launch_seq_out(int M, long long N, const void* X, const double* S, double* out, cudaStream_t st);
+// outer Krylov vector kernels (at most 8 vectors per launch)
+struct VecList {
+    const double* v[8];
+};
+struct Coefs {
+    double c[8];
+};
+int krylov_grid();
+// part[j * krylov_grid() + b] = block b's partial sum of <V_j, w>, j < k
+cudaError_t launch_mdot(const VecList& V, int k, const double* w, long long n, double* part, cudaStream_t st);
+// y = beta y + sum_{j<k} c_j V_j  (beta = 0: y is not read)
+cudaError_t launch_maxpy(const VecList& V, const Coefs& c, int k, double beta, double* y, long long n,
+                         cudaStream_t st);
+// r = (u0 stacked in block 0) + b - Cu  (u0, b may be null)
+cudaError_t launch_w_minus(const double* u0, const double* b, const double* Cu, double* r, int L, int M,
+                           long long N, cudaStream_t st);
 template <typename R> cudaError_t launch_gmres(const GmresArgs& a, void* scratch, cudaStream_t st);
 // bytes of Krylov vectors per system (basis of restart + 1 vectors and x)
 size_t gmres_vector_bytes(int restart, long long N, size_t csize);

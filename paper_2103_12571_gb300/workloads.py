@@ -119,5 +119,6 @@ def heat_forcing_samples(n, times):
 
 
 def heat_forcing_u0(n):
-    """u(pi) of the solution cos(t) phi (see the design doc on the printed forcing)."""
+    """u(pi) of cos(t) phi, the exact solution under the printed forcing
+    (substitution gives cos t, not the printed sin t)."""
     return np.cos(HEAT_T0) * heat_forcing_field(n)
