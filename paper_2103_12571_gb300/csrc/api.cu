@@ -280,12 +280,6 @@ static int run_spatial(ac_plan* p, void* X, const void* mu_dT, int planes, int t
     sa.tw_y = p->tw_y;
     sa.rows_per_block = p->rows_per_block;
     sa.cols_per_block = p->cols_per_block;
-    if (p->spatial_path == 2) {
-        // few planes (sequential stepping): smaller tiles, so that each pass
-        // still has two CTAs per SM
-        while (sa.rows_per_block > 1 && (long)planes * sa.ny / sa.rows_per_block < 2 * 152) sa.rows_per_block >>= 1;
-        while (sa.cols_per_block > 2 && (long)planes * sa.nx / sa.cols_per_block < 2 * 152) sa.cols_per_block >>= 1;
-    }
     if (p->spatial_path == 0) {
         CK(ac::launch_space_1d<R>(sa, st));
         p->launches++;
