@@ -58,3 +58,22 @@ def test_krylov_converges_where_richardson_cannot():
     u, st = plan.krylov_solve(to_dev(torch, u0), 1e-12, restart=20)
     assert st["converged"] and st["iters"] <= 40, st
     assert rel2(u.cpu().numpy(), ref) < 1e-10
+
+
+def test_krylov_cap_and_zero_rhs():
+    """The step cap ends the solve with AC_ERR_NO_CONVERGENCE (u holds the
+    last iterate, stats its history); a zero right-hand side returns u = 0."""
+    torch = torch_cuda()
+    from paper_2103_12571_gb300 import _lib
+    from paper_2103_12571_gb300.api import Plan
+    prob = workloads.problem(1, 64, nu=0.1, order=2, M=2, L=8, T=0.1)
+    plan = Plan(prob, precision="c128", max_iter=3)
+    u0 = to_dev(torch, np.random.default_rng(43).standard_normal(64))
+    u, st = plan.krylov_solve(u0, 1e-30, restart=2, raise_on_fail=False)
+    assert st["iters"] == 3 and not st["converged"]
+    assert st["res_rel"][3] < st["res_rel"][0]
+    with pytest.raises(_lib.ACError) as e:
+        plan.krylov_solve(u0, 1e-30, restart=2)
+    assert e.value.code == _lib.AC_ERR_NO_CONVERGENCE
+    z, st = plan.krylov_solve(torch.zeros_like(u0), 1e-12)
+    assert st["converged"] and float(z.abs().max()) == 0.0

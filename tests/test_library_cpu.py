@@ -141,3 +141,18 @@ def test_host_stencil_taps_reject_unsupported(api):
             api.stencil_taps(workloads.problem(1, 32, nu=0.1, cx=1.0, order=order, upwind=upwind))
         with pytest.raises(ACError):
             api.Plan(workloads.problem(1, 32, nu=0.1, cx=1.0, order=order, upwind=upwind, M=2, L=4))
+
+
+def test_new_entry_points_reject_null_arguments(api):
+    """Argument checks of the C ABI run before any device work (no GPU)."""
+    from paper_2103_12571_gb300 import _lib
+    L = _lib.lib()
+    st = _lib.Stats()
+    assert L.ac_sequential_solve(None, None, None, None, None) == _lib.AC_ERR_INVALID_ARG
+    assert L.ac_krylov_solve(None, None, None, None, 0, ctypes.c_double(1e-10), 10, ctypes.byref(st),
+                             None) == _lib.AC_ERR_INVALID_ARG
+    assert L.ac_window_solve(None, None, 1, None, None, ctypes.c_double(1e-10), None, None, None) == \
+        _lib.AC_ERR_INVALID_ARG
+    assert L.ac_stencil_taps(None, None, None, None) == _lib.AC_ERR_INVALID_ARG
+    msg = L.ac_last_error()
+    assert msg is not None
