@@ -299,6 +299,19 @@ def run_ours(args):
     dom = max(kern, key=lambda k: kern[k][0])
     dom_ms = kern[dom][0] / kern[dom][1]
     roof = roofline(dom, dom_ms, D, L, M, N)
+    # algorithmic HBM bytes of each kernel group per step and their share of
+    # the measured copy bandwidth (the FP64-bound residual kernel included)
+    F = L // 2 + 1
+    alg = {"resid_tfft_mix": 8.0 * D + F * M * N * 8, "spatial_solve": 6.0 * F * M * N * 8,
+           "mix_tifft_update": F * M * N * 8 + 16.0 * D}
+    hbm_peak = roof["peak"] if roof["unit"] == "GB/s" else \
+        json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0)
+    hbm_per_kernel = {}
+    for k, b in alg.items():
+        if k in kern and kern[k][1]:
+            t = kern[k][0] / kern[k][1]
+            hbm_per_kernel[k] = {"algorithmic_bytes": b, "ms": round(t, 4), "gbs": round(b / (t * 1e-3) / 1e9, 1),
+                                 "frac_of_measured_hbm": round(b / (t * 1e-3) / 1e9 / hbm_peak, 3)}
     out = {
         "metric": "space-time DoF*iterations/s (one alpha-circulant Richardson iteration, mixed FP64/c64)",
         "value": value, "unit": "DoF*it/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -315,6 +328,7 @@ def run_ours(args):
         "sequential_baseline": seq,
         "all_configs": configs,
         "roofline": roof,
+        "hbm_per_kernel": hbm_per_kernel,
         "clocks": clk,
         "wall_s_timed": wall,
     }

@@ -75,10 +75,18 @@ __device__ __forceinline__ R cos16(int k) {
 
 template <typename C, bool INV>
 __device__ __forceinline__ C rot(C a, int k, int n) {
-    // a * exp(-+2 pi i k / n), n in {2, 4, 8, 16}
+    // a * exp(-+2 pi i k / n), n in {2, 4, 8, 16}.  Rotations by -1 and -+i
+    // are exact swaps and negations: without fast-math the compiler keeps
+    // multiplications by 0.0 and 1.0, which would cost real FMAs.
     typedef decltype(a.x) R;
-    if (k == 0) return a;
-    const int kk = k * (16 / n);
+    const int kk = (k * (16 / n)) & 15;
+    if (kk == 0) return a;
+    if (kk == 8) return cmake(-a.x, -a.y);
+    if (kk == 4 || kk == 12) {
+        // exp(-i pi/2) = -i (forward, kk = 4); the other three cases by symmetry
+        const bool minus_i = (kk == 4) != INV;
+        return minus_i ? cmake(a.y, -a.x) : cmake(-a.y, a.x);
+    }
     const R c = cos16<R>(kk);
     const R s = INV ? cos16<R>(kk + 12) : -cos16<R>(kk + 12);   // -+ sin(2 pi kk / 16)
     C r;
