@@ -898,12 +898,13 @@ int ac_setup(const ac_problem* prob, int M, int L, double dT, const ac_alpha_sch
     // 18% faster); on larger grids halving the tile measured slower.
     int Pu = P;
     while (Pu > 8 && (p->N + Pu - 1) / Pu < 3 * 152) Pu >>= 1;
-    // The residual kernel is FP64-bound.  In complex64 plans a half-size tile
-    // (twice the CTAs) lets its FP64 phase overlap better with the transform
-    // phases of other CTAs: 2-3% on the 2D heat (64 -> 32 points) and 1D
-    // advection (16 -> 8) workloads; tiles under 8 points and complex128 plans
+    // The residual kernel is FP64-bound.  In complex64 plans smaller tiles
+    // (more CTAs) let its FP64 phase overlap better with the transform phases
+    // of other CTAs: a quarter of tiles of 64 points and more (2D heat 256^2:
+    // 64 -> 16 points, 6% faster than 64), half of tiles of 16 to 32 points
+    // (1D advection: 16 -> 8, 3%); tiles under 8 points and complex128 plans
     // measured slower.
-    p->P = (precision == AC_C64 && P >= 16) ? P / 2 : P;
+    p->P = precision != AC_C64 ? P : (P >= 64 ? P / 4 : (P >= 16 ? P / 2 : P));
     p->grid = (p->N + p->P - 1) / p->P;
     p->P_upd = Pu;
     p->grid_upd = (p->N + Pu - 1) / Pu;
