@@ -404,6 +404,13 @@ static int precond_a(ac_plan* p, const double* u, const double* u0, const double
     return stage_a<float>(p, u, u0, b, b_rev, transposed, st, record_res, recompute, fwd_only);
 }
 
+// the spatial solves alone (after a precond_a with fwd_only)
+static int precond_space(ac_plan* p, int transposed, cudaStream_t st) {
+    ProfScope ps(p, KK_SPACE, st);
+    if (p->precision == AC_C128) return run_spatial<double>(p, p->X, p->d_mu, p->F * p->M, transposed, true, st);
+    return run_spatial<float>(p, p->X, p->d_mu, p->F * p->M, transposed, true, st);
+}
+
 static int precond_b(ac_plan* p, double* out, int accumulate, cudaStream_t st, int diff_last = 0) {
     if (p->precision == AC_C128) return stage_b<double>(p, out, accumulate, st, diff_last);
     return stage_b<float>(p, out, accumulate, st, diff_last);
@@ -599,8 +606,17 @@ static int richardson_loop(ac_plan* p, const double* u0, const double* b, int b_
         if (rc) return rc;
         // residual of u^(k), transform and spatial solve; the host reads the
         // residual norm while the spatial solve runs and only then queues the
-        // update, so a converged u^(k) is returned unchanged
-        rc = precond_a(p, u, u0, b, b_rev, transposed, st, true);
+        // update, so a converged u^(k) is returned unchanged.  The spatial
+        // solve is queued before the norm is known, except when the residual
+        // is predicted to meet tol (the last two residuals extrapolated
+        // geometrically): then it would be wasted, and it is queued only if the
+        // prediction fails.
+        bool speculate = true;
+        if (sc.stop_rule == AC_STOP_RESIDUAL && k >= 2 && S->res_rel[k - 2] > 0.0) {
+            const double pred = S->res_rel[k - 1] * (S->res_rel[k - 1] / S->res_rel[k - 2]);
+            speculate = !(pred <= tol);
+        }
+        rc = precond_a(p, u, u0, b, b_rev, transposed, st, true, 0, !speculate);
         if (rc) return rc;
         CK(cudaEventSynchronize(p->ev_res));
         if (k > 0 && p->spatial_path >= 3) S->inner_iters[k - 1] = inner_summary(p, &S->inner_failed[k - 1]);
@@ -630,6 +646,10 @@ static int richardson_loop(ac_plan* p, const double* u0, const double* b, int b_
         } else grew = 0;
         prev_res = res;
         S->alpha[k] = alpha;
+        if (!speculate) {
+            rc = precond_space(p, transposed, st);
+            if (rc) return rc;
+        }
         rc = precond_b(p, u, 1, st);
         if (rc) return rc;
         if (sc.mode == AC_ALPHA_PAPER) m = m_next;
