@@ -95,10 +95,39 @@ __device__ __forceinline__ C rot(C a, int k, int n) {
     return r;
 }
 
+// Complex add, subtract and multiply for the transforms.  In FP64 they are
+// written as FMAs whose operands are all registers (one = 1.0, zero = 0.0
+// loaded at run time): on this GPU such DFMAs issue about 16% faster than
+// DADD and DMUL, and a * 1 + b, a * b + 0 round exactly like a + b, a * b.
+// In FP32 the plain operations run at full rate.
+template <typename C, typename R>
+__device__ __forceinline__ C xadd(C a, C b, R one) {
+    if constexpr (sizeof(R) == 8) return cmake(fma(a.x, one, b.x), fma(a.y, one, b.y));
+    else return cadd(a, b);
+}
+template <typename C, typename R>
+__device__ __forceinline__ C xsub(C a, C b, R one) {
+    if constexpr (sizeof(R) == 8) return cmake(fma(-b.x, one, a.x), fma(-b.y, one, a.y));
+    else return csub(a, b);
+}
+// a * b, or a * conj(b) (CONJ)
+template <bool CONJ, typename C, typename R>
+__device__ __forceinline__ C xmul(C a, C b, R zero) {
+    if constexpr (sizeof(R) == 8) {
+        const R by = CONJ ? -b.y : b.y;
+        C r;
+        r.x = fma(a.x, b.x, fma(-a.y, by, zero));
+        r.y = fma(a.x, by, fma(a.y, b.x, zero));
+        return r;
+    } else {
+        return CONJ ? cmulc(a, b) : cmul(a, b);
+    }
+}
+
 // In-register R-point DFT (forward: y_r = sum_q x_q w_R^{qr}; INV: conjugate),
-// natural order in and out.
-template <int R, bool INV, typename C>
-__device__ __forceinline__ void small_dft(C* v) {
+// natural order in and out.  one: a register holding 1.0 (see xadd).
+template <int R, bool INV, typename C, typename RR>
+__device__ __forceinline__ void small_dft(C* v, RR one) {
 #pragma unroll
     for (int h = R / 2; h >= 1; h >>= 1) {
 #pragma unroll
@@ -106,8 +135,8 @@ __device__ __forceinline__ void small_dft(C* v) {
 #pragma unroll
             for (int k = 0; k < h; ++k) {
                 C a = v[j0 + k], b = v[j0 + k + h];
-                v[j0 + k] = cadd(a, b);
-                v[j0 + k + h] = rot<C, INV>(csub(a, b), k, 2 * h);
+                v[j0 + k] = xadd(a, b, one);
+                v[j0 + k + h] = rot<C, INV>(xsub(a, b, one), k, 2 * h);
             }
         }
     }
@@ -152,6 +181,10 @@ __device__ __forceinline__ void fft_stage(C* data, int logn, int logns, int logb
 #pragma unroll
             for (int r = 1; r < R; ++r) w[r] = tw[(j * r) << twshift];
         }
+        // tw[0] = 1 - 0i: register copies of 1 and 0 for the FP64 FMA forms
+        const C w0 = tw[0];
+        const auto one = w0.x;
+        const auto zero = w0.y;
         // shared-memory offsets fit in 32 bits
         C* p = data + (base * js + b * bs);
         const int mjs = m * js;
@@ -161,17 +194,17 @@ __device__ __forceinline__ void fft_stage(C* data, int logn, int logns, int logb
 #pragma unroll
             for (int r = 0; r < R; ++r) v[r] = p[r * mjs + mm * ms];
             if (!INV) {
-                small_dft<R, false>(v);
+                small_dft<R, false>(v, one);
                 if (!UNIT) {
 #pragma unroll
-                    for (int r = 1; r < R; ++r) v[r] = cmul(v[r], w[r]);
+                    for (int r = 1; r < R; ++r) v[r] = xmul<false>(v[r], w[r], zero);
                 }
             } else {
                 if (!UNIT) {
 #pragma unroll
-                    for (int r = 1; r < R; ++r) v[r] = cmulc(v[r], w[r]);
+                    for (int r = 1; r < R; ++r) v[r] = xmul<true>(v[r], w[r], zero);
                 }
-                small_dft<R, true>(v);
+                small_dft<R, true>(v, one);
             }
 #pragma unroll
             for (int r = 0; r < R; ++r) p[r * mjs + mm * ms] = v[r];
