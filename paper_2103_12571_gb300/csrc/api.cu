@@ -683,7 +683,14 @@ static int ensure_seq_tables(ac_plan* p, cudaStream_t st) {
         e = cudaMemcpyAsync(p->d_seq_Sinv, Sinv.data(), sizeof(cd) * M * M, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = upload_c(p, p->d_seq_mu, lam.data(), lam.size(), st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return fail(AC_ERR_CUDA, "sequential tables: %s", cudaGetErrorString(e));
+    if (e != cudaSuccess) {
+        // leave no partial state behind: the next call starts over
+        for (void** b : {(void**)&p->d_seq_S, (void**)&p->d_seq_Sinv, &p->d_seq_mu}) {
+            if (*b) cudaFree(*b);
+            *b = nullptr;
+        }
+        return fail(AC_ERR_CUDA, "sequential tables: %s", cudaGetErrorString(e));
+    }
     return AC_OK;
 }
 
