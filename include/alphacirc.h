@@ -135,8 +135,13 @@ typedef struct ac_plan ac_plan;
 /* Builds the host tables (Radau IIA nodes and Q of eq. (collocation), stencil
  * coefficients and symbols, FFT twiddles) and allocates the device workspace
  * (F*M*N complex plus small tables) on the current CUDA device.
- * M >= 1 (<= 4), L a power of two (2..1024), dT > 0.  Writes *out.
- * Errors: AC_ERR_INVALID_ARG for unsupported sizes, AC_ERR_CUDA. */
+ * M >= 1 (<= 4), L a power of two (2..1024) with L*M small enough for the
+ * shared-memory time transform, dT > 0, a supported stencil scheme (see
+ * ac_problem).  precision: AC_C128 or AC_C64.  inner: AC_INNER_FFT needs
+ * power-of-two nx (and ny) and a 1D grid of at most 160 KB of transform values
+ * per plane; AC_INNER_BICGSTAB and AC_INNER_GMRES take any grid with at least
+ * 2 * radius + 1 points per axis.  Writes *out.
+ * Errors: AC_ERR_INVALID_ARG for unsupported sizes or schemes, AC_ERR_CUDA. */
 int ac_setup(const ac_problem* prob, int M, int L, double dT,
              const ac_alpha_schedule* sched, int precision, int inner,
              ac_plan** out);
