@@ -60,3 +60,20 @@ def test_implicit_euler_adjoint():
     lam, st = Plan(prob, precision="c128", alpha="paper").adjoint_solve(to_dev(torch, g), tol=1e-14,
                                                                          raise_on_fail=False)
     assert rel2(lam.cpu().numpy(), ref) < 1e-11, st
+
+
+def test_non_finite_right_hand_side_is_reported():
+    """A NaN in u0 (or in the adjoint's g) makes ||w|| non-finite: the solves
+    fail with AC_ERR_NOT_FINITE before iterating."""
+    torch = torch_cuda()
+    from paper_2103_12571_gb300 import _lib
+    from paper_2103_12571_gb300.api import Plan
+    prob = workloads.problem(1, 64, nu=0.1, order=2, M=2, L=4, T=0.1)
+    plan = Plan(prob, precision="c64", alpha="mixed")
+    u0 = to_dev(torch, np.random.default_rng(24).standard_normal(64))
+    u0[5] = float("nan")
+    for call in (lambda: plan.solve(u0, 1e-10), lambda: plan.krylov_solve(u0, 1e-10),
+                 lambda: plan.adjoint_solve(u0.repeat(8).reshape(4, 2, 64).contiguous(), 1e-10)):
+        with pytest.raises(_lib.ACError) as e:
+            call()
+        assert e.value.code == _lib.AC_ERR_NOT_FINITE
