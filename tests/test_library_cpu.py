@@ -26,7 +26,7 @@ def declared_symbols():
         if f.endswith(".h"):
             txt = open(os.path.join(inc, f)).read()
             txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-            names |= set(re.findall(r"\b(ac_[a-z_0-9]+)\s*\(", txt))
+            names |= set(re.findall(r"\b(ac_[A-Za-z_0-9]+)\s*\(", txt))
     return sorted(names)
 
 
@@ -156,3 +156,10 @@ def test_new_entry_points_reject_null_arguments(api):
     assert L.ac_stencil_taps(None, None, None, None) == _lib.AC_ERR_INVALID_ARG
     msg = L.ac_last_error()
     assert msg is not None
+
+
+def test_binding_declares_every_header_function(api):
+    """Every function the header declares has a ctypes prototype in the
+    binding (so no call goes through ctypes' default int conversions)."""
+    from paper_2103_12571_gb300 import _lib
+    assert sorted(declared_symbols()) == sorted(_lib._PROTOS)

@@ -281,6 +281,17 @@ def test_sequential_equals_fourier_closed_form_2d_advdiff():
     np.testing.assert_allclose(sel[(3, 0)], seq[3, 0], atol=1e-13)
 
 
+@pytest.mark.parametrize("order", [1, 3, 5])
+def test_sequential_equals_fourier_closed_form_upwind(order):
+    """The oracle's two routes agree for upwind stencils (sparse matrix of the
+    mirrored stencil for the negative velocity, and its symbol)."""
+    prob = workloads.problem(2, 16, 12, nu=0.02, cx=0.8, cy=-0.6, order=order, M=3, L=6, T=0.1, upwind=True)
+    t, Q, A, dT = setup(prob)
+    u0 = workloads.random_phase_bumps_2d(16, 12, 3.0, seed=4)
+    seq = sequential.sequential_solve(A, Q, dT, prob["L"], u0)
+    np.testing.assert_allclose(seq, fourier.modal_solution(u0, prob, Q, dT, prob["L"]), atol=1e-13)
+
+
 # --------------------------------------------- stability function and order
 def test_stability_function_is_pade():
     z = np.array([-0.3, -5.0 + 2j, 0.2j, -40.0, -1e-3])
