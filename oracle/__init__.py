@@ -13,9 +13,12 @@ method using diagonalization", arXiv 2103.12571):
 
 * ``collocation``  - Radau IIA nodes and the collocation matrix Q (Sec. 2.1,
                      eq. (collocation); node polynomial of Sec. 2.3).
-* ``operators``    - periodic central-difference operators A, C_coll, H and
-                     the all-at-once matrices C and C_alpha (eqs. (Hm),
-                     (globalsys), (prec)).
+* ``stencils``     - finite-difference weights of the centred (orders 2, 4,
+                     6) and upwind (orders 1..5) schemes of Sec. 5, from their
+                     moment conditions in exact rational arithmetic.
+* ``operators``    - periodic stencil operators A, C_coll, H and the
+                     all-at-once matrices C and C_alpha (eqs. (Hm),
+                     (globalsys), (prec)), and the forcing term v_l.
 * ``sequential``   - the sequential collocation time-stepper (eq.
                      (seq_collocation_problem)), its discrete adjoint and the
                      gradient contractions.  This is THE oracle: the unique
@@ -35,4 +38,4 @@ brute-force dense solve.  Functions without such a pin are marked
 "parity unpinned" in their docstring (none at present).
 """
 
-from . import collocation, operators, sequential, paradiag, alpha_rule, fourier  # noqa: F401
+from . import collocation, stencils, operators, sequential, paradiag, alpha_rule, fourier  # noqa: F401
