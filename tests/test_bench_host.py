@@ -41,3 +41,20 @@ def test_traffic_is_null_when_the_kernel_sources_changed(monkeypatch):
     assert bench.measured_traffic("k_fwd") == t["kernels"]["k_fwd"]
     monkeypatch.setattr(bench, "source_hash", lambda: "0" * 64)
     assert bench.measured_traffic("k_fwd") is None
+
+
+def test_reference_arm_prints_the_contract_line():
+    """`bench.py --impl reference` times the CPU oracle (no GPU) and prints one
+    JSON line with the reference keys."""
+    import subprocess
+    import sys
+    out = subprocess.run([sys.executable, os.path.join(bench.ROOT, "bench.py"), "--impl", "reference",
+                          "--steps", "1", "--warmup", "1"], capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = [l for l in out.stdout.splitlines() if l.startswith("{")][-1]
+    d = json.loads(line)
+    assert d["impl"] == "reference" and d["value"] > 0 and d["unit"] == "DoF*it/s"
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["cpu_baseline"]["cores"] >= 1 and d["cpu_baseline"]["sample"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+    assert d["config"]["workload"] == "heat2d_256x256_M3_L64" and d["higher_is_better"] is True
