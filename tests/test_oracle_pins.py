@@ -90,6 +90,26 @@ def test_lemma2_roots_are_eigenvalues(M):
         np.testing.assert_allclose(roots, ev, atol=1e-11)
 
 
+@pytest.mark.parametrize("M", [1, 2, 3, 4])
+def test_QGinv_is_Q_times_dense_inverse_of_G(M):
+    # eq. (QGL): Q G_l^{-1} with G_l = I + d_l H_M (Lemma 1's eigenvalues d_l).
+    # Pinned against a dense inverse of G_l and against Lemma 2's roots.
+    t = collocation.radau_iia_nodes(M)
+    Q = collocation.collocation_matrix(t)
+    H = collocation.H_matrix(M)
+    for L, alpha in ((8, 1e-3), (16, 0.3)):
+        for d in paradiag.eigenvalues_d(L, alpha):
+            B = paradiag.QGinv(Q, t, d)
+            G = np.eye(M) + d * H
+            np.testing.assert_allclose(B @ G, Q, atol=1e-14)
+            np.testing.assert_allclose(B, Q @ np.linalg.inv(G), atol=1e-13)
+            r = d / (1 + d)
+            roots = list(np.roots(paradiag.lemma2_char_poly(t, r)[::-1]))
+            for ev in np.linalg.eigvals(B):   # the same multiset
+                j = int(np.argmin([abs(ev - z) for z in roots]))
+                assert abs(ev - roots.pop(j)) < 1e-10
+
+
 def test_lemma2_printed_sign_is_the_other_shift():
     # The lemma as printed (c_0 = (r+1) b_0, minus sign in c_m) gives the
     # spectrum of Q + r D_t H_M, i.e. eq. (QGL) with r -> -r.
@@ -410,7 +430,48 @@ def test_alpha_sequence_reproduces_fig1():
 def test_alpha_sequence_limit():
     alphas, ms = alpha_rule.alpha_sequence(1.0, 1e-10, kmax=60)
     assert abs(ms[-1] - 4e-10) < 1e-15 and abs(alphas[-1] - 0.5) < 1e-9
-    assert alpha_rule.gamma(64, 2.0 ** -53, 0.0, 2.0) == 64 * 3 * 2.0 ** -53 * 2.0
+
+
+@pytest.mark.parametrize("L", [8, 32])
+@pytest.mark.parametrize("alpha", [0.5, 1e-2])
+@pytest.mark.parametrize("tau", [1e-6, 1e-9])
+@pytest.mark.parametrize("scale", [1.0, 1e3])
+def test_gamma_is_theorem2_error_of_an_inexact_preconditioner(L, alpha, tau, scale):
+    """gamma / alpha is Theorem 2's bound (eq. (errr1)) on the error one
+    preconditioner application makes when every block solve of eq. (s2) is
+    inexact with relative residual tau (kappa(B) ~ 1, ||r|| = ||w||).
+
+    Scalar problem u' = lam u with dT lam = -1 (C_coll = 2, so
+    ||B^{-1}||_inf <= 1), r = scale * (1, ..., 1).  The block residuals are
+    given size tau ||x||_inf and phases that add up coherently in the last
+    step: the measured error then lies between gamma / 3 (attained: the sum
+    of the L frequency contributions, each at least tau ||x|| / (3 L) after
+    the inverse transform, times alpha^{-(L-1)/L} ||x||_inf >= L) and
+    ||B^{-1}|| gamma / alpha (the theorem).  A gamma without the factor L,
+    without tau or without the norm of w fails one side."""
+    Q = collocation.collocation_matrix(collocation.radau_iia_nodes(1))
+    A = np.array([[-1.0]])
+    import scipy.sparse as sp
+    A = sp.csr_matrix(A)
+    dT = 1.0
+    r = scale * np.ones((L, 1, 1))
+    x = paradiag.time_forward(r.astype(np.complex128), alpha)
+    d = paradiag.eigenvalues_d(L, alpha)
+    B = np.array([paradiag.block_matrix(A, Q, dT, dk).toarray()[0, 0] for dk in d])
+    xinf = np.max(np.abs(x))
+    # exact preconditioner and the inexact one (B_k (y_k + dy_k) = x_k + rho_k)
+    g = np.exp(2j * np.pi * (L - 1) * np.arange(L) / L) / B
+    rho = tau * xinf * np.conj(g) / np.abs(g)
+    dy = (rho / B).reshape(L, 1, 1)
+    du = paradiag.time_inverse(dy, alpha)
+    err = np.max(np.abs(du))
+    nB = np.max(1.0 / np.abs(B))
+    kappa = np.max(np.abs(B)) * nB
+    eps = 2.0 ** -53
+    upper = nB / (1 - eps * kappa) * alpha_rule.gamma(L, eps * kappa, tau, scale) / alpha
+    lower = alpha_rule.gamma(L, 0.0, tau, scale) / 3.0
+    assert nB <= 1.0 + 1e-15
+    assert lower <= err <= upper, (lower, err, upper)
 
 
 def test_algorithm2_driver_stops_on_last_block_difference():
