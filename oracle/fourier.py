@@ -104,3 +104,67 @@ def contraction_factor(z, alpha, L, Q):
     with the recursion above."""
     R = stability_function(z, Q)
     return -alpha * R ** L / (1.0 - alpha * R ** L)
+
+
+def modal_blocks(u0, prob, Q, dT, L):
+    """The closed form above one block at a time: yields (l, m, u_lm) for
+    l = 0..L-1, m = 0..M-1 (0-based), keeping only R^l uhat_0 between
+    blocks, so that full-size problems can be compared block by block."""
+    z = dT * symbol(prob)
+    s = stage_vector(z, Q)
+    R = s[..., -1]
+    uh = _fwd(np.asarray(u0, np.float64), prob)
+    M = Q.shape[0]
+    for l in range(L):
+        for m in range(M):
+            yield l, m, _inv(s[..., m] * uh, prob).real
+        uh = uh * R
+
+
+def _symbol_parts(prob):
+    """(d sigma / d nu, d sigma / d cx, d sigma / d cy) on the fft layout of
+    ``symbol``: sigma = nu Lap_hat - cx Dx_hat - cy Dy_hat (upwind
+    derivatives biased by the sign of their own velocity component)."""
+    nx, lx, order = prob["nx"], prob.get("lx", 1.0), prob["order"]
+    up = bool(prob.get("upwind", False))
+    cx, cy = prob.get("cx", 0.0), prob.get("cy", 0.0)
+    lap_x = symbol_d2(nx, lx, order, up)
+    d1x = symbol_d1(nx, lx, order, up, cx)
+    if prob["dim"] == 1:
+        return lap_x, -d1x, np.zeros_like(d1x)
+    ny, ly = prob["ny"], prob.get("ly", 1.0)
+    lap_y = symbol_d2(ny, ly, order, up)
+    d1y = symbol_d1(ny, ly, order, up, cy)
+    shape = (ny, nx)
+    return (lap_y[:, None] + lap_x[None, :],
+            np.broadcast_to(-d1x[None, :], shape), np.broadcast_to(-d1y[:, None], shape))
+
+
+def last_node_loss_gradients(u0, target, prob, Q, dT, L):
+    """J = ||u_{L,M} - target||_2^2 (last node of the last step) and its
+    gradients (dJ/du0, dJ/dnu, dJ/dcx, dJ/dcy) from the closed form
+        uhat_{L,M} = R(z)^L uhat_0,  z = dT sigma(k),
+        dR/dz = e_M^T (I - z Q)^{-1} Q (I - z Q)^{-1} 1_M,
+    with Parseval's identity for the numpy DFT (sum |x|^2 = sum |X|^2 / N).
+    The derivative of J through the periodic, constant-coefficient
+    collocation stepping, written mode by mode (an oracle independent of the
+    sequential adjoint)."""
+    u0 = np.asarray(u0, np.float64)
+    N = u0.shape[0]
+    z = dT * symbol(prob)
+    s = stage_vector(z, Q)
+    R = s[..., -1]
+    M = Q.shape[0]
+    Az = np.eye(M) - z[..., None, None] * Q
+    dR = np.linalg.solve(Az, (Q @ s[..., None]))[..., -1, 0]
+    u0h = _fwd(u0, prob)
+    RL = R ** L
+    uLh = RL * u0h
+    uL = _inv(uLh, prob).real
+    res = uL - np.asarray(target, np.float64)
+    J = float(res @ res)
+    resh = _fwd(res, prob)
+    du0 = 2.0 * _inv(np.conj(RL) * resh, prob).real
+    base = L * R ** (L - 1) * dR * dT * u0h
+    grads = [float(2.0 / N * np.real(np.sum(np.conj(resh) * base * ds))) for ds in _symbol_parts(prob)]
+    return J, du0, grads[0], np.array(grads[1:])

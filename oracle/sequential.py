@@ -24,20 +24,45 @@ import scipy.sparse.linalg as spla
 from .operators import C_coll, operator_parts
 
 
+# C_coll has a symmetric sparsity pattern (Q is dense, A a periodic stencil):
+# minimum-degree ordering on A^T + A keeps the fill of the LU factors small.
+ORDERING = "MMD_AT_PLUS_A"
+
+
+def factor(A, Q, dT, dtype=np.float64):
+    """Sparse LU of C_coll = I - dT Q (x) A."""
+    return spla.splu(C_coll(A, Q, dT).tocsc().astype(dtype), permc_spec=ORDERING)
+
+
+class Stepper:
+    """The forward sweep one step at a time: C_coll u_l = H u_{l-1} (+ v_l),
+    with u_{-1} standing for u_0 (so the first right-hand side is u_0 stacked
+    over the M nodes)."""
+
+    def __init__(self, A, Q, dT, u0, dtype=np.float64):
+        self.M, self.N = Q.shape[0], A.shape[0]
+        self.lu = factor(A, Q, dT, dtype)
+        self.last = np.asarray(u0, dtype=dtype)   # u_{l-1, M}, or u_0 before the first step
+        self.dtype = dtype
+
+    def step(self, v_l=None):
+        rhs = np.tile(self.last, self.M)
+        if v_l is not None:
+            rhs = rhs + v_l.reshape(-1)
+        u_l = self.lu.solve(rhs).reshape(self.M, self.N)
+        self.last = u_l[self.M - 1]
+        return u_l
+
+
 def sequential_solve(A, Q, dT, L, u0, v=None):
     """u of shape (L, M, N): one sparse LU of C_coll, then L forward/back
     substitutions.  v (optional, shape (L, M, N)) is the forcing block v_l."""
     M, N = Q.shape[0], A.shape[0]
     dtype = np.result_type(np.asarray(u0).dtype, A.dtype, np.float64)
-    lu = spla.splu(C_coll(A, Q, dT).tocsc().astype(dtype))
+    st = Stepper(A, Q, dT, u0, dtype)
     u = np.empty((L, M, N), dtype=dtype)
-    rhs = np.tile(np.asarray(u0, dtype=dtype), M)
     for l in range(L):
-        if l > 0:
-            rhs = np.tile(u[l - 1, M - 1], M)
-        if v is not None:
-            rhs = rhs + v[l].reshape(-1)
-        u[l] = lu.solve(rhs).reshape(M, N)
+        u[l] = st.step(None if v is None else v[l])
     return u
 
 
@@ -46,7 +71,7 @@ def sequential_solve_general(A, Q, dT, w):
     by the same forward sweep: C_coll u_l = w_l + H u_{l-1}."""
     L, M, N = w.shape
     dtype = np.result_type(w.dtype, A.dtype, np.float64)
-    lu = spla.splu(C_coll(A, Q, dT).tocsc().astype(dtype))
+    lu = factor(A, Q, dT, dtype)
     u = np.empty((L, M, N), dtype=dtype)
     for l in range(L):
         rhs = w[l].astype(dtype).copy()
@@ -60,7 +85,7 @@ def sequential_adjoint(A, Q, dT, g):
     """lam = C^{-T} g by the backward sweep above; g of shape (L, M, N)."""
     L, M, N = g.shape
     dtype = np.result_type(g.dtype, A.dtype, np.float64)
-    lu = spla.splu(C_coll(A, Q, dT).tocsc().astype(dtype))
+    lu = factor(A, Q, dT, dtype)
     lam = np.empty((L, M, N), dtype=dtype)
     for l in range(L - 1, -1, -1):
         rhs = g[l].astype(dtype).copy()

@@ -313,6 +313,49 @@ def test_sequential_equals_fourier_closed_form_upwind(order):
 
 
 # --------------------------------------------- stability function and order
+def test_modal_blocks_equal_modal_solution():
+    prob = small_prob(dim=2, nx=8, ny=4, nu=0.3, cx=0.7, cy=-0.4, M=3, L=5, T=0.3)
+    t, Q, A, dT = setup(prob)
+    u0 = np.random.default_rng(4).standard_normal(32)
+    full = fourier.modal_solution(u0, prob, Q, dT, 5)
+    seen = 0
+    for l, m, blk in fourier.modal_blocks(u0, prob, Q, dT, 5):
+        np.testing.assert_allclose(blk, full[l, m], atol=1e-14)
+        seen += 1
+    assert seen == 15
+
+
+@pytest.mark.parametrize("dim,order,upwind,cx,cy", [(1, 2, False, 0.8, 0.0), (2, 2, False, 1.0, 0.5),
+                                                    (2, 4, False, -0.6, 0.3), (2, 3, True, 0.9, -0.7)])
+def test_closed_form_loss_gradients_equal_sequential_adjoint(dim, order, upwind, cx, cy):
+    """The closed-form gradients of J = ||u_{L,M} - target||^2 against the
+    sequential discrete adjoint (sparse LU, backward sweep) and against
+    central differences of the closed-form loss."""
+    prob = workloads.problem(dim, 12, 8, nu=0.05, cx=cx, cy=cy, order=order, M=3, L=6, T=0.3, upwind=upwind)
+    t, Q, A, dT = setup(prob)
+    N = operators.n_points(prob)
+    rng = np.random.default_rng(9)
+    u0, target = rng.standard_normal(N), rng.standard_normal(N)
+    J, du0, dnu, dc = fourier.last_node_loss_gradients(u0, target, prob, Q, dT, 6)
+    u = sequential.sequential_solve(A, Q, dT, 6, u0)
+    assert abs(J - np.sum((u[-1, -1] - target) ** 2)) < 1e-12 * J
+    g = np.zeros_like(u)
+    g[-1, -1] = 2 * (u[-1, -1] - target)
+    lam = sequential.sequential_adjoint(A, Q, dT, g)
+    du0_s, dnu_s, dc_s = sequential.grad_params(prob, Q, dT, u, lam)
+    np.testing.assert_allclose(du0, du0_s, rtol=0, atol=1e-11 * np.max(np.abs(du0_s)))
+    assert abs(dnu - dnu_s) < 1e-10 * max(1.0, abs(dnu_s))
+    np.testing.assert_allclose(dc[: dim], dc_s[: dim], rtol=1e-10, atol=1e-12)
+    h = 1e-6
+    for key, val in (("nu", dnu), ("cx", dc[0])) + ((("cy", dc[1]),) if dim == 2 else ()):
+        pp, pm = dict(prob), dict(prob)
+        pp[key] += h
+        pm[key] -= h
+        Jp = fourier.last_node_loss_gradients(u0, target, pp, Q, dT, 6)[0]
+        Jm = fourier.last_node_loss_gradients(u0, target, pm, Q, dT, 6)[0]
+        assert abs((Jp - Jm) / (2 * h) - val) < 1e-6 * max(1.0, abs(val)), key
+
+
 def test_stability_function_is_pade():
     z = np.array([-0.3, -5.0 + 2j, 0.2j, -40.0, -1e-3])
     Q2 = collocation.collocation_matrix(collocation.radau_iia_nodes(2))
