@@ -265,14 +265,18 @@ int ac_grad_params(ac_plan* plan, const double* u, const double* lam,
 /* ---- preconditioner solve without device allocation --------------------- */
 
 /* No counterpart in the paper.  e = C_alpha^{-1} r exactly as ac_precond_solve
- * computes it (same kernels, same precision choices), for callers that cannot
+ * computes it (the same kernels, tiles, spatial path and tables as a plan that
+ * ac_setup builds for the same problem with AC_INNER_FFT), for callers that cannot
  * allocate device memory when they need a solve -- e.g. code whose device
  * memory is entirely owned by another framework's caching allocator, or a
  * latency-critical loop that must not pay for the implicit synchronisation of
  * cudaMalloc/cudaFree.  No plan is needed and nothing is allocated: every
  * buffer and table the solve uses is carved out of one fixed 32 MiB device
  * array inside this library, which each GPU that loads the library keeps
- * until the process exits.
+ * until the process exits.  The small tables (twiddles, symbols, eigenbases)
+ * are uploaded on every call from pageable host memory, so the host waits
+ * until the work queued before the call on `stream` has finished; the
+ * kernels are then queued without further waits.
  *   prob, M, L, dT: as for ac_setup (FFT inner solve, power-of-two grid, L a
  *     power of two in 2..1024, M in 1..4); precision: AC_C128 or AC_C64.
  *   alpha in (0,1).  r, e: device, L*M*N doubles (may be the same buffer).
@@ -328,6 +332,14 @@ int ac_profile_enable(ac_plan* plan, int on);
  * Synchronises the device.  Returns the number of kernel kinds. */
 int ac_profile_read(ac_plan* plan, int cap, const char** names, double* ms,
                     long long* count);
+
+/* FP64 FMA throughput of the current device, measured with a kernel of
+ * independent register-operand FMA chains (8 per thread, 8 CTAs of 256
+ * threads per SM), best of three CUDA-event timed launches.  Writes FMAs per
+ * second to *fma_per_s (host).  Instrumentation for the roofline of the
+ * FP64-bound kernels; no counterpart in the paper.  Allocates and frees a
+ * few bytes of device memory and synchronises the stream. */
+int ac_measure_fp64_fma_rate(double* fma_per_s, void* stream);
 
 const char* ac_status_string(int status);
 const char* ac_last_error(void);

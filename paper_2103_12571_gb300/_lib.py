@@ -80,6 +80,7 @@ _PROTOS = {
     "ac_freq_tables": (_I, [_I, _I, _D, _I, _P, _P, _P, _P]),
     "ac_alpha_sequence": (_I, [_D, _D, _I, _P, _P]),
     "ac_profile_enable": (_I, [_P, _I]),
+    "ac_measure_fp64_fma_rate": (_I, [_P, _P]),
     "ac_profile_read": (_I, [_P, _I, ctypes.POINTER(ctypes.c_char_p), _P, _P]),
     "ac_status_string": (ctypes.c_char_p, [_I]),
     "ac_last_error": (ctypes.c_char_p, []),

@@ -75,6 +75,12 @@ class Plan:
             C.lib().ac_destroy(h)
             self._h = None
 
+    def params(self):
+        """[nu, cx, cy] of the plan's spatial operator (cy = 0 in 1D)."""
+        p = self.prob
+        return [float(p.get("nu", 0.0)), float(p.get("cx", 0.0)),
+                float(p.get("cy", 0.0)) if int(p["dim"]) == 2 else 0.0]
+
     @property
     def shape(self):
         return (self.L, self.M, self.N)
@@ -189,6 +195,13 @@ class Plan:
         return {names[i].decode(): (ms[i], cnt[i]) for i in range(min(n, cap))}
 
 
+def measure_fp64_fma_rate():
+    """FP64 FMAs per second of the current device (instrumentation)."""
+    r = ctypes.c_double(0.0)
+    C.check(C.lib().ac_measure_fp64_fma_rate(ctypes.byref(r), _stream()), "ac_measure_fp64_fma_rate")
+    return r.value
+
+
 # ------------------------------------------------------------------ host planner
 def radau_nodes(M):
     t = np.zeros(M)
@@ -242,6 +255,11 @@ class RichardsonSolve(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, u0, params, plan, tol):
+        plan_params = plan.params()
+        given = [float(v) for v in params.detach().cpu().reshape(-1).tolist()]
+        if len(given) != 3 or given != plan_params:
+            raise ValueError("params %s differ from the plan's (nu, cx, cy) = %s: build the plan for these values"
+                             % (given, plan_params))
         u, st = plan.solve(u0.contiguous(), tol)
         ctx.plan, ctx.tol = plan, tol
         ctx.save_for_backward(u)

@@ -14,6 +14,7 @@
 
 #include "alphacirc.h"
 #include "kernels.h"
+#include "norm2.cuh"
 #include "planner.h"
 
 namespace ac {
@@ -23,6 +24,7 @@ cudaError_t launch_fill_stack(const double* u0, double* u, int L, int M, long lo
 cudaError_t launch_a_inf(const Grid& g, const double* u0, double* part, int grid, cudaStream_t st);
 cudaError_t launch_colloc_rhs(const double* b, const double* dtQ, double* v, int L, int M, long long N,
                               cudaStream_t st);
+cudaError_t launch_dfma_rate(const double* ab, int rounds, double* sink, int grid, cudaStream_t st);
 }
 
 using ac::cd;
@@ -50,9 +52,11 @@ void ac_internal_set_error(const char* msg) { g_err = msg; }
                         __FILE__, __LINE__);                                                  \
     } while (0)
 
-enum KernelKind { KK_FWD = 0, KK_SPACE, KK_UPD, KK_APPLY, KK_GRAD, KK_AUX, KK_COUNT };
+// Profiler kinds.  KK_SPACE_ROWS / KK_SPACE_COLS time the launches of the
+// three-pass 2D spatial solve one by one (inside the KK_SPACE group).
+enum KernelKind { KK_FWD = 0, KK_SPACE, KK_UPD, KK_APPLY, KK_GRAD, KK_AUX, KK_SPACE_ROWS, KK_SPACE_COLS, KK_COUNT };
 static const char* kKindNames[KK_COUNT] = {"resid_tfft_mix", "spatial_solve", "mix_tifft_update",
-                                           "apply_C", "grad_contract", "aux"};
+                                           "apply_C", "grad_contract", "aux", "space_rows", "space_cols"};
 
 struct EventPair {
     int kind;
@@ -84,21 +88,23 @@ struct ac_plan {
     void* sigT_y = nullptr;
     double* d_qs = nullptr;
     double* d_s = nullptr;
-    float* d_inv_s_w = nullptr;
+    float2* d_wnorm = nullptr;   // [L] 2^20 / (s_l w_scale) as float pairs (residual norm)
     double* d_sinv = nullptr;
     void* d_Sinv = nullptr;
     void* d_P = nullptr;
     void* d_mu = nullptr;
-    float* d_part_fwd = nullptr;
-    float* d_part_upd = nullptr;
+    double* d_part_fwd = nullptr;
+    double* d_part_upd = nullptr;
     double* d_part_d = nullptr;  // FP64 reductions
     double* d_dtQ = nullptr;     // dT Q
     double* d_dtQT = nullptr;    // dT Q^T
     void* d_bicg = nullptr;      // Krylov vectors when they do not fit in shared memory
+    double2* d_mu64 = nullptr;   // complex64 BiCGStab: dT mu in FP64 (reliable updates)
+    double2* d_x64 = nullptr;    // complex64 BiCGStab: FP64 solution accumulators, F*M*N
     int* d_iters = nullptr;      // Krylov iterations per system
     int* h_iters = nullptr;      // pinned copy
-    float* h_part_fwd = nullptr;  // pinned
-    float* h_part_upd = nullptr;
+    double* h_part_fwd = nullptr;  // pinned
+    double* h_part_upd = nullptr;
     double* h_part_d = nullptr;
     int part_d_len = 0;
     // table cache key
@@ -147,7 +153,7 @@ struct ProfScope {
     cudaStream_t st;
     cudaEvent_t a = nullptr;
     ProfScope(ac_plan* p_, int k, cudaStream_t s) : p(p_), kind(k), st(s) {
-        if (p->prof) {
+        if (p->prof && kind >= 0) {
             a = get_event(p);
             cudaEventRecord(a, st);
         }
@@ -200,44 +206,25 @@ static cudaError_t upload_c(const ac_plan* p, void* dst, const cd* src, size_t n
     return cudaMemcpyAsync(dst, tmp.data(), tmp.size() * sizeof(float), cudaMemcpyHostToDevice, st);
 }
 
-// w_n^k = exp(-2 pi i k / n), k < n (the full circle: the mixed-radix
-// stages index it with j * r)
-static void twiddles(int n, std::vector<cd>& tw) {
-    tw.resize(n);
-    for (int k = 0; k < n; ++k) tw[k] = std::exp(cd(0.0, -2.0 * M_PI * k / n));
-}
-
-// Alpha-dependent tables: qs, s, inv_s_w, sinv (FP64/FP32) and the per-frequency
-// Sinv, P, dT mu (transform precision).
+// Alpha-dependent tables (ac::alpha_tables): qs, s, the residual-norm
+// weights, sinv (FP64 / float pairs) and the per-frequency Sinv, P, dT mu
+// (transform precision).
 static int ensure_tables(ac_plan* p, double alpha, int transposed, double wscale, cudaStream_t st) {
     if (alpha == p->cur_alpha && transposed == p->cur_transposed && wscale == p->cur_wscale) return AC_OK;
     if (!(alpha > 0.0) || !(alpha < 1.0)) return fail(AC_ERR_INVALID_ARG, "alpha must be in (0,1), got %g", alpha);
-    const int L = p->L, M = p->M, F = p->F;
-    std::vector<double> qs((size_t)L * M * M), s(L), sinv(L);
-    std::vector<float> isw(L);
-    for (int l = 0; l < L; ++l) {
-        s[l] = (l == 0) ? 1.0 : std::pow(alpha, (double)l / L);
-        sinv[l] = ((l == 0) ? 1.0 : std::pow(alpha, -(double)l / L)) / L;
-        isw[l] = (float)(1.0 / (s[l] * wscale));
-        for (int m = 0; m < M; ++m)
-            for (int j = 0; j < M; ++j)
-                qs[((size_t)l * M + m) * M + j] =
-                    s[l] * p->dT * (transposed ? p->Q[j * M + m] : p->Q[m * M + j]);
-    }
-    std::vector<cd> mu((size_t)F * M), Sinv((size_t)F * M * M), P((size_t)F * M * M);
-    double worst = ac::freq_tables(M, L, alpha, transposed != 0, p->Q, p->t, mu.data(), Sinv.data(),
-                                   P.data(), nullptr);
-    if (worst < 0 || worst > 1e10)
+    ac::AlphaTables T;
+    if (!ac::alpha_tables(p->M, p->L, p->dT, p->Q, p->t, alpha, transposed != 0, wscale, &T))
         return fail(AC_ERR_NOT_DIAGONALIZABLE, "Q G_l^{-1} not diagonalisable for alpha=%g (cond %g)", alpha,
-                    worst);
-    for (auto& v : mu) v *= p->dT;
-    CK(cudaMemcpyAsync(p->d_qs, qs.data(), qs.size() * sizeof(double), cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(p->d_s, s.data(), s.size() * sizeof(double), cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(p->d_sinv, sinv.data(), sinv.size() * sizeof(double), cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(p->d_inv_s_w, isw.data(), isw.size() * sizeof(float), cudaMemcpyHostToDevice, st));
-    CK(upload_c(p, p->d_Sinv, Sinv.data(), Sinv.size(), st));
-    CK(upload_c(p, p->d_P, P.data(), P.size(), st));
-    CK(upload_c(p, p->d_mu, mu.data(), mu.size(), st));
+                    T.worst_cond);
+    CK(cudaMemcpyAsync(p->d_qs, T.qs.data(), T.qs.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(p->d_s, T.s.data(), T.s.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(p->d_sinv, T.sinv.data(), T.sinv.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(p->d_wnorm, T.wnorm.data(), T.wnorm.size() * sizeof(float), cudaMemcpyHostToDevice, st));
+    CK(upload_c(p, p->d_Sinv, T.Sinv.data(), T.Sinv.size(), st));
+    CK(upload_c(p, p->d_P, T.P.data(), T.P.size(), st));
+    CK(upload_c(p, p->d_mu, T.mu_dT.data(), T.mu_dT.size(), st));
+    if (p->d_mu64)
+        CK(cudaMemcpyAsync(p->d_mu64, T.mu_dT.data(), T.mu_dT.size() * sizeof(cd), cudaMemcpyHostToDevice, st));
     p->cur_alpha = alpha;
     p->cur_transposed = transposed;
     p->cur_wscale = wscale;
@@ -252,11 +239,15 @@ static int gmres_restart(const ac_plan* p) {
     return std::min(m, 32);
 }
 
-static double inner_tau(const ac_plan* p) {
+static double inner_tau(const ac_plan* p, bool reliable = false) {
     double tau = p->sched.tau > 0 ? p->sched.tau : 1e-8;
-    if (p->precision == AC_C64) tau = std::max(tau, std::ldexp(1.0, -20));
+    if (p->precision == AC_C64 && !reliable) tau = std::max(tau, std::ldexp(1.0, -20));
     return tau;
 }
+
+// complex64 BiCGStab inside the preconditioner runs with FP64 reliable
+// updates and honours tau below the FP32 floor
+static bool bicg_reliable(const ac_plan* p) { return p->spatial_path == 3 && p->d_mu64 && p->d_x64; }
 
 // The shifted spatial solves of eq. (d2), (I - mu dT A) x = X_plane, in place
 // on `planes` planes of N complex values with per-plane shifts mu_dT, by the
@@ -264,7 +255,7 @@ static double inner_tau(const ac_plan* p) {
 // host (a stream-ordered copy; off inside graph capture).
 template <typename R>
 static int run_spatial(ac_plan* p, void* X, const void* mu_dT, int planes, int transposed, bool fetch_iters,
-                       cudaStream_t st) {
+                       cudaStream_t st, bool prof_passes = false) {
     ac::SpaceArgs sa{};
     sa.nx = p->prob.nx;
     sa.ny = p->prob.dim == 2 ? p->prob.ny : 1;
@@ -287,9 +278,19 @@ static int run_spatial(ac_plan* p, void* X, const void* mu_dT, int planes, int t
         CK(ac::launch_space_2d_small<R>(sa, st));
         p->launches++;
     } else if (p->spatial_path == 2) {
-        CK(ac::launch_space_rows<R>(sa, 0, st));
-        CK(ac::launch_space_cols<R>(sa, st));
-        CK(ac::launch_space_rows<R>(sa, 1, st));
+        const bool pp = prof_passes && p->prof;
+        {
+            ProfScope ps(p, pp ? KK_SPACE_ROWS : -1, st);
+            CK(ac::launch_space_rows<R>(sa, 0, st));
+        }
+        {
+            ProfScope ps(p, pp ? KK_SPACE_COLS : -1, st);
+            CK(ac::launch_space_cols<R>(sa, st));
+        }
+        {
+            ProfScope ps(p, pp ? KK_SPACE_ROWS : -1, st);
+            CK(ac::launch_space_rows<R>(sa, 1, st));
+        }
         p->launches += 3;
     } else if (p->spatial_path == 3) {
         ac::BicgArgs ba{};
@@ -297,10 +298,13 @@ static int run_spatial(ac_plan* p, void* X, const void* mu_dT, int planes, int t
         ba.planes = planes;
         ba.M = p->M;
         ba.max_iter = p->sched.inner_max_iter > 0 ? p->sched.inner_max_iter : 4000;
-        ba.tau = inner_tau(p);
+        const bool rel = bicg_reliable(p) && mu_dT == p->d_mu;
+        ba.tau = inner_tau(p, rel);
         ba.X = X;
         ba.mu_dT = mu_dT;
         ba.iters = p->d_iters;
+        ba.mu64 = rel ? p->d_mu64 : nullptr;
+        ba.x64 = rel ? p->d_x64 : nullptr;
         CK(ac::launch_bicgstab<R>(ba, p->d_bicg, st));
         p->launches++;
         if (fetch_iters)
@@ -347,7 +351,7 @@ static int stage_a(ac_plan* p, const double* u, const double* u0, const double* 
     fa.alpha = p->cur_alpha;
     fa.qs = p->d_qs;
     fa.s = p->d_s;
-    fa.inv_s_w = p->d_inv_s_w;
+    fa.wnorm = p->d_wnorm;
     fa.tw = p->tw_L;
     fa.Sinv = p->d_Sinv;
     fa.X = p->X;
@@ -359,13 +363,13 @@ static int stage_a(ac_plan* p, const double* u, const double* u0, const double* 
         p->launches++;
     }
     if (record_res) {
-        CK(cudaMemcpyAsync(p->h_part_fwd, p->d_part_fwd, sizeof(float) * p->grid, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(p->h_part_fwd, p->d_part_fwd, sizeof(double) * p->grid, cudaMemcpyDeviceToHost, st));
         CK(cudaEventRecord(p->ev_res, st));
     }
     if (fwd_only) return AC_OK;
     {
         ProfScope ps(p, KK_SPACE, st);
-        int rc = run_spatial<R>(p, p->X, p->d_mu, p->F * p->M, transposed, true, st);
+        int rc = run_spatial<R>(p, p->X, p->d_mu, p->F * p->M, transposed, true, st, true);
         if (rc) return rc;
     }
     return AC_OK;
@@ -407,8 +411,9 @@ static int precond_a(ac_plan* p, const double* u, const double* u0, const double
 // the spatial solves alone (after a precond_a with fwd_only)
 static int precond_space(ac_plan* p, int transposed, cudaStream_t st) {
     ProfScope ps(p, KK_SPACE, st);
-    if (p->precision == AC_C128) return run_spatial<double>(p, p->X, p->d_mu, p->F * p->M, transposed, true, st);
-    return run_spatial<float>(p, p->X, p->d_mu, p->F * p->M, transposed, true, st);
+    if (p->precision == AC_C128)
+        return run_spatial<double>(p, p->X, p->d_mu, p->F * p->M, transposed, true, st, true);
+    return run_spatial<float>(p, p->X, p->d_mu, p->F * p->M, transposed, true, st, true);
 }
 
 static int precond_b(ac_plan* p, double* out, int accumulate, cudaStream_t st, int diff_last = 0) {
@@ -424,7 +429,7 @@ static int residual_only(ac_plan* p, const double* u, const double* u0, const do
     CK(cudaEventSynchronize(p->ev_res));
     double s = 0.0;
     for (int i = 0; i < p->grid; ++i) s += p->h_part_fwd[i];
-    *res = std::sqrt(s) * wscale / wn2;
+    *res = std::sqrt(s) * (wscale / ac::kNormPrescale) / wn2;
     return AC_OK;
 }
 
@@ -527,7 +532,7 @@ static int richardson_loop(ac_plan* p, const double* u0, const double* b, int b_
     const ac_alpha_schedule& sc = p->sched;
     const int max_iter = std::min(std::max(sc.max_iter, 1), AC_MAX_STATS - 1);
     const double eps = p->precision == AC_C128 ? std::ldexp(1.0, -53) : std::ldexp(1.0, -24);
-    const double tau = p->inner != AC_INNER_FFT ? inner_tau(p) : 0.0;
+    const double tau = p->inner != AC_INNER_FFT ? inner_tau(p, bicg_reliable(p)) : 0.0;
     const double gam = p->L * (3.0 * eps + tau) * winf;
     // m0 ~ ||u^(0) - u*||_inf: T max|u_t(0)| = T ||A u0 + b||_inf (Sec. 3.3, the
     // Lipschitz estimate) when the caller gives none; for a zero initial
@@ -567,10 +572,12 @@ static int richardson_loop(ac_plan* p, const double* u0, const double* b, int b_
             if (rc) return rc;
             rc = precond_b(p, u, 0, st, 1);
             if (rc) return rc;
-            CK(cudaMemcpyAsync(p->h_part_upd, p->d_part_upd, sizeof(float) * p->grid_upd, cudaMemcpyDeviceToHost, st));
+            CK(cudaMemcpyAsync(p->h_part_upd, p->d_part_upd, sizeof(double) * p->grid_upd, cudaMemcpyDeviceToHost, st));
             CK(cudaStreamSynchronize(st));
-            float mx = 0.f;
+            double mx = 0.0;
             for (int i = 0; i < p->grid_upd; ++i) mx = std::max(mx, p->h_part_upd[i]);
+            for (int i = 0; i < p->grid_upd; ++i)
+                if (std::isnan(p->h_part_upd[i])) mx = p->h_part_upd[i];
             S->alpha[k] = alpha;
             S->m[k] = sc.mode == AC_ALPHA_PAPER ? m : 0.0;
             S->diff_last[k] = mx;
@@ -592,15 +599,23 @@ static int richardson_loop(ac_plan* p, const double* u0, const double* b, int b_
     }
     int grew = 0;
     double prev_res = 1e300;
+    // Safeguard of the adaptive rules: the correction-form alpha assumes inner
+    // solves that meet tau.  When the residual grows, they evidently did not
+    // (Krylov inner solves stall where the shifted systems are badly
+    // conditioned, and their condition number grows with alpha), so alpha is
+    // cut to a quarter from that iteration on (growth by more than a factor 2,
+    // so that fluctuations at the attainable floor do not shrink alpha).
+    double alpha_scale = 1.0;
     for (int k = 0;; ++k) {
         double alpha;
         double m_next = 0.0;
+        const double cap = alpha_mixed * alpha_scale;
         if (sc.mode == AC_ALPHA_FIXED) alpha = sc.alpha0;
-        else if (sc.mode == AC_ALPHA_MIXED) alpha = alpha_mixed;
+        else if (sc.mode == AC_ALPHA_MIXED) alpha = cap;
         else {
             alpha = std::sqrt(gam / m);          // alpha_{k+1} = sqrt(gamma / m_k)
             m_next = 2.0 * std::sqrt(m * gam);   // m_{k+1} = 2 sqrt(m_k gamma)
-            alpha = std::min(alpha_mixed, std::max(alpha, 1e-12));
+            alpha = std::min(cap, std::max(alpha, 1e-12));
         }
         rc = ensure_tables(p, alpha, transposed, wscale, st);
         if (rc) return rc;
@@ -622,7 +637,7 @@ static int richardson_loop(ac_plan* p, const double* u0, const double* b, int b_
         if (k > 0 && p->spatial_path >= 3) S->inner_iters[k - 1] = inner_summary(p, &S->inner_failed[k - 1]);
         double s = 0.0;
         for (int i = 0; i < p->grid; ++i) s += p->h_part_fwd[i];
-        const double res = std::sqrt(s) * wscale / wn2;
+        const double res = std::sqrt(s) * (wscale / ac::kNormPrescale) / wn2;
         S->res_rel[k] = res;
         S->m[k] = sc.mode == AC_ALPHA_PAPER ? m : 0.0;
         S->iters = k;
@@ -643,6 +658,18 @@ static int richardson_loop(ac_plan* p, const double* u0, const double* b, int b_
                 CK(cudaStreamSynchronize(st));
                 return fail(AC_ERR_NO_CONVERGENCE, "residual grew three times in a row (iteration %d)", k);
             }
+            if (sc.mode != AC_ALPHA_FIXED && res > 2.0 * prev_res) {
+                // a real blow-up (not noise at the attainable floor): redo this
+                // iteration's transform and spatial solve with a quarter of alpha
+                alpha_scale *= 0.25;
+                alpha = sc.mode == AC_ALPHA_MIXED ? alpha_mixed * alpha_scale
+                                                  : std::min(alpha_mixed * alpha_scale, alpha);
+                rc = ensure_tables(p, alpha, transposed, wscale, st);
+                if (rc) return rc;
+                rc = precond_a(p, u, u0, b, b_rev, transposed, st, false, 0, false);
+                if (rc) return rc;
+                speculate = true;   // the spatial solve is queued
+            }
         } else grew = 0;
         prev_res = res;
         S->alpha[k] = alpha;
@@ -654,10 +681,12 @@ static int richardson_loop(ac_plan* p, const double* u0, const double* b, int b_
         if (rc) return rc;
         if (sc.mode == AC_ALPHA_PAPER) m = m_next;
         if (sc.stop_rule == AC_STOP_PAPER) {
-            CK(cudaMemcpyAsync(p->h_part_upd, p->d_part_upd, sizeof(float) * p->grid_upd, cudaMemcpyDeviceToHost, st));
+            CK(cudaMemcpyAsync(p->h_part_upd, p->d_part_upd, sizeof(double) * p->grid_upd, cudaMemcpyDeviceToHost, st));
             CK(cudaStreamSynchronize(st));
-            float mx = 0.f;
+            double mx = 0.0;
             for (int i = 0; i < p->grid_upd; ++i) mx = std::max(mx, p->h_part_upd[i]);
+            for (int i = 0; i < p->grid_upd; ++i)
+                if (std::isnan(p->h_part_upd[i])) mx = p->h_part_upd[i];
             S->diff_last[k] = mx;
         }
     }
@@ -789,9 +818,9 @@ void ac_destroy(ac_plan* p) {
     drain_profile(p);
     for (auto e : p->pool) cudaEventDestroy(e);
     void* bufs[] = {p->X, p->tw_L, p->tw_x, p->tw_y, p->sig_x, p->sig_y, p->sigT_x, p->sigT_y,
-                    p->d_qs, p->d_s, p->d_inv_s_w, p->d_sinv, p->d_Sinv, p->d_P, p->d_mu,
+                    p->d_qs, p->d_s, p->d_wnorm, p->d_sinv, p->d_Sinv, p->d_P, p->d_mu,
                     p->d_part_fwd, p->d_part_upd, p->d_part_d, p->d_dtQ, p->d_dtQT, p->d_bicg,
-                    p->d_iters};
+                    p->d_iters, p->d_mu64, p->d_x64};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (p->h_part_fwd) cudaFreeHost(p->h_part_fwd);
@@ -874,67 +903,20 @@ int ac_setup(const ac_problem* prob, int M, int L, double dT, const ac_alpha_sch
         p->d2y[i] = sten.d2y[i];
     }
 
-    // spatial solve path
+    // spatial solve path and kernel tiles
     const size_t cs = p->csize;
-    if (inner == AC_INNER_FFT) {
-        if (!is_pow2(prob->nx) || !is_pow2(ny)) {
-            ac_destroy(p);
-            return fail(AC_ERR_INVALID_ARG, "the FFT inner solver needs power-of-two grid sizes");
-        }
-        if (prob->dim == 1) {
-            if ((size_t)prob->nx * cs > 160 * 1024) {
-                ac_destroy(p);
-                return fail(AC_ERR_INVALID_ARG, "1D grid too large for the one-CTA FFT solve");
-            }
-            p->spatial_path = 0;
-        } else if ((size_t)prob->nx * ny * cs <= 160 * 1024) {
-            p->spatial_path = 1;
-        } else {
-            p->spatial_path = 2;
-            int rpb = std::max(1, (int)(32768 / ((size_t)prob->nx * cs)));
-            while (rpb & (rpb - 1)) rpb &= rpb - 1;
-            p->rows_per_block = std::min(rpb, ny);
-            int W = (int)(128 / cs);
-            if (W > prob->nx) W = prob->nx;
-            p->cols_per_block = W;
-            if ((size_t)prob->nx * cs > 160 * 1024 || (size_t)ny * W * cs > 160 * 1024) {
-                ac_destroy(p);
-                return fail(AC_ERR_INVALID_ARG, "2D grid too large for the three-pass FFT solve");
-            }
-        }
-    } else {
-        p->spatial_path = inner == AC_INNER_GMRES ? 4 : 3;
-        const int rad = sten.rad;
-        if (prob->nx < 2 * rad + 1 || (prob->dim == 2 && ny < 2 * rad + 1)) {
-            ac_destroy(p);
-            return fail(AC_ERR_INVALID_ARG, "grid smaller than the stencil");
-        }
-    }
-
-    // tile of the time kernels: P points, L*M*P reals of shared memory
-    const size_t rsz = cs / 2;
-    int P = 256;
-    while (P > 2 && (size_t)L * M * P * rsz > 50 * 1024) P >>= 1;
-    while (P > 16 && (p->N + P - 1) / P < 2 * 152) P >>= 1;
-    if ((size_t)L * M * P * rsz > 200 * 1024) {
+    ac::PlanShape shape;
+    if (const char* why = ac::plan_shape(p->prob, M, L, precision, inner, sten.rad, &shape)) {
         ac_destroy(p);
-        return fail(AC_ERR_INVALID_ARG, "L*M too large for the shared-memory time transform");
+        return fail(AC_ERR_INVALID_ARG, "%s", why);
     }
-    // The update kernel is latency-bound: smaller tiles while its grid has
-    // fewer than three CTAs per SM (1D advection, 4096 points: 16 -> 8 points,
-    // 18% faster); on larger grids halving the tile measured slower.
-    int Pu = P;
-    while (Pu > 8 && (p->N + Pu - 1) / Pu < 3 * 152) Pu >>= 1;
-    // The residual kernel is FP64-bound.  In complex64 plans smaller tiles
-    // (more CTAs) let its FP64 phase overlap better with the transform phases
-    // of other CTAs: a quarter of tiles of 64 points and more (2D heat 256^2:
-    // 64 -> 16 points, 6% faster than 64), half of tiles of 16 to 32 points
-    // (1D advection: 16 -> 8, 3%); tiles under 8 points and complex128 plans
-    // measured slower.
-    p->P = precision != AC_C64 ? P : (P >= 64 ? P / 4 : (P >= 16 ? P / 2 : P));
-    p->grid = (p->N + p->P - 1) / p->P;
-    p->P_upd = Pu;
-    p->grid_upd = (p->N + Pu - 1) / Pu;
+    p->spatial_path = shape.spatial_path;
+    p->rows_per_block = shape.rows_per_block;
+    p->cols_per_block = shape.cols_per_block;
+    p->P = shape.P;
+    p->grid = shape.grid;
+    p->P_upd = shape.P_upd;
+    p->grid_upd = shape.grid_upd;
 
     // device buffers
     cudaError_t e = cudaSuccess;
@@ -953,13 +935,13 @@ int ac_setup(const ac_problem* prob, int M, int L, double dT, const ac_alpha_sch
     AL(p->sigT_y, (size_t)ny * cs);
     AL(p->d_qs, sizeof(double) * (size_t)L * M * M);
     AL(p->d_s, sizeof(double) * L);
-    AL(p->d_inv_s_w, sizeof(float) * L);
+    AL(p->d_wnorm, sizeof(float2) * L);
     AL(p->d_sinv, sizeof(double) * L);
     AL(p->d_Sinv, (size_t)F * M * M * cs);
     AL(p->d_P, (size_t)F * M * M * cs);
     AL(p->d_mu, (size_t)F * M * cs);
-    AL(p->d_part_fwd, sizeof(float) * p->grid);
-    AL(p->d_part_upd, sizeof(float) * p->grid_upd);
+    AL(p->d_part_fwd, sizeof(double) * p->grid);
+    AL(p->d_part_upd, sizeof(double) * p->grid_upd);
     p->part_d_len = std::max(2 * 152 * 2, 3 * 152 * 4);
     AL(p->d_part_d, sizeof(double) * p->part_d_len);
     AL(p->d_dtQ, sizeof(double) * M * M);
@@ -967,14 +949,18 @@ int ac_setup(const ac_problem* prob, int M, int L, double dT, const ac_alpha_sch
     if (p->spatial_path == 3) {
         AL(p->d_iters, sizeof(int) * F * M);
         if (6 * cs * (size_t)p->N > 200 * 1024) AL(p->d_bicg, 6 * cs * (size_t)p->N * F * M);
+        if (precision == AC_C64) {
+            AL(p->d_mu64, sizeof(double2) * F * M);
+            AL(p->d_x64, sizeof(double2) * (size_t)p->N * F * M);
+        }
     } else if (p->spatial_path == 4) {
         AL(p->d_iters, sizeof(int) * F * M);
         const size_t per = ac::gmres_vector_bytes(gmres_restart(p), p->N, cs);
         if (per > 160 * 1024) AL(p->d_bicg, per * F * M);
     }
 #undef AL
-    if (e == cudaSuccess) e = cudaMallocHost((void**)&p->h_part_fwd, sizeof(float) * p->grid);
-    if (e == cudaSuccess) e = cudaMallocHost((void**)&p->h_part_upd, sizeof(float) * p->grid_upd);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&p->h_part_fwd, sizeof(double) * p->grid);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&p->h_part_upd, sizeof(double) * p->grid_upd);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&p->h_part_d, sizeof(double) * p->part_d_len);
     if (e == cudaSuccess && p->spatial_path >= 3) e = cudaMallocHost((void**)&p->h_iters, sizeof(int) * F * M);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_res, cudaEventDisableTiming);  // spin: low latency
@@ -990,11 +976,11 @@ int ac_setup(const ac_problem* prob, int M, int L, double dT, const ac_alpha_sch
         if (rc == AC_OK && upload_c(p, dst, v.data(), v.size(), 0) != cudaSuccess)
             rc = fail(AC_ERR_CUDA, "table upload failed");
     };
-    twiddles(L, tw);
+    ac::twiddles(L, tw);
     up(p->tw_L, tw);
-    twiddles(prob->nx, tw);
+    ac::twiddles(prob->nx, tw);
     up(p->tw_x, tw);
-    twiddles(ny, tw);
+    ac::twiddles(ny, tw);
     up(p->tw_y, tw);
     ac::axis_symbol(prob->nx, p->grid_fwd.tx, sx.data());
     ac::axis_symbol(prob->nx, p->grid_adj.tx, sxT.data());
@@ -1098,7 +1084,7 @@ int ac_richardson_step(ac_plan* p, double alpha, const double* u0, const double*
         CK(cudaEventSynchronize(p->ev_res));
         double s = 0.0;
         for (int i = 0; i < p->grid; ++i) s += p->h_part_fwd[i];
-        *res_rel_out = wn2 > 0 ? std::sqrt(s) * wscale / wn2 : std::sqrt(s) * wscale;
+        *res_rel_out = wn2 > 0 ? std::sqrt(s) * (wscale / ac::kNormPrescale) / wn2 : std::sqrt(s) * (wscale / ac::kNormPrescale);
     }
     return AC_OK;
 }
@@ -1200,7 +1186,7 @@ int ac_krylov_solve(ac_plan* p, const double* u0, const double* b, double* u, in
     }
     // the preconditioner's alpha: the fixed one, else the correction-form rule
     const double eps = p->precision == AC_C128 ? std::ldexp(1.0, -53) : std::ldexp(1.0, -24);
-    const double tau = p->inner != AC_INNER_FFT ? inner_tau(p) : 0.0;
+    const double tau = p->inner != AC_INNER_FFT ? inner_tau(p, bicg_reliable(p)) : 0.0;
     const double alpha = p->sched.mode == AC_ALPHA_FIXED
                              ? p->sched.alpha0
                              : std::min(0.25, std::max(1e-8, std::sqrt(p->L * (3.0 * eps + tau))));
@@ -1356,6 +1342,39 @@ int ac_grad_params(ac_plan* p, const double* u, const double* lam, double* du0, 
     dparams[0] = s[0];
     dparams[1] = -s[1];
     dparams[2] = p->prob.dim == 2 ? -s[2] : 0.0;
+    return AC_OK;
+}
+
+int ac_measure_fp64_fma_rate(double* fma_per_s, void* stream) {
+    if (!fma_per_s) return fail(AC_ERR_INVALID_ARG, "null argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0, sms = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int grid = 8 * sms, rounds = 8192;
+    double* buf = nullptr;
+    CK(cudaMalloc((void**)&buf, sizeof(double) * (4 + grid)));
+    const double ab[3] = {0.999999, 1e-6, 1234.5678};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaMemcpyAsync(buf, ab, sizeof(ab), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = ac::launch_dfma_rate(buf, rounds, buf + 4, grid, st);   // warm-up
+    float best = 0.f;
+    for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+        e = cudaEventRecord(e0, st);
+        if (e == cudaSuccess) e = ac::launch_dfma_rate(buf, rounds, buf + 4, grid, st);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && (best == 0.f || ms < best)) best = ms;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(buf);
+    if (e != cudaSuccess) return fail(AC_ERR_CUDA, "FP64 rate probe: %s", cudaGetErrorString(e));
+    *fma_per_s = (double)grid * 256.0 * 8.0 * rounds / (best * 1e-3);
     return AC_OK;
 }
 

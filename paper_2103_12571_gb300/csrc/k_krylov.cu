@@ -6,7 +6,15 @@
 // the vectors in shared memory when they fit, else in a global scratch slice:
 //
 // k_bicgstab: BiCGStab.  Per iteration two stencil products and three fused
-//   block reductions (<r0, v>; <t, s>, <t, t>; <r0, r>, <r, r>).  The loop is
+//   block reductions (<r0, v>; <t, s>, <t, t>; <r0, r>, <r, r>).  In
+//   complex64 the recursively updated residual drifts away from the true one
+//   once it falls below about kappa * eps_32, and the iteration stalls there;
+//   with FP64 reliable updates (mu64 and x64 given) the solution is kept in an
+//   FP64 accumulator, and whenever the recursive residual has dropped tenfold
+//   since the last update (or meets tau) the update so far is added to it and
+//   the residual is replaced by b - (I - mu A) x computed in FP64.  The
+//   iteration continues with that residual, and convergence is decided on
+//   it, so complex64 solves reach tolerances below the FP32 floor.  The loop is
 //   bounded by max_iter and stops early when the residual has not dropped
 //   below 0.99 of its best value for 256 iterations (stagnation at the
 //   precision floor).  A near-breakdown of the bi-orthogonality (|<r0, v>|
@@ -62,6 +70,33 @@ __device__ __forceinline__ void apply_shifted(const Grid& g, C mu, const C* __re
     }
 }
 
+// (A x)_i in FP64 for the reliable updates
+__device__ __forceinline__ double2 stencil_fp64(const Grid& g, const double2* __restrict__ x, int i) {
+    const int nx = g.nx;
+    const int iy = i / nx, ix = i - iy * nx;
+    const double2 c = x[i];
+    double ax = g.c0 * c.x, ay = g.c0 * c.y;
+#pragma unroll
+    for (int o = 0; o < 6; ++o) {
+        if (o < 2 * g.rad) {
+            const int tap = stencil_tap(o);
+            int jx = ix + stencil_offset(o);
+            jx = jx < 0 ? jx + nx : (jx >= nx ? jx - nx : jx);
+            const double2 xv = x[iy * nx + jx];
+            ax = fma(g.tx[tap], xv.x, ax);
+            ay = fma(g.tx[tap], xv.y, ay);
+            if (g.dim == 2) {
+                int jy = iy + stencil_offset(o);
+                jy = jy < 0 ? jy + g.ny : (jy >= g.ny ? jy - g.ny : jy);
+                const double2 yv = x[jy * nx + ix];
+                ax = fma(g.ty[tap], yv.x, ax);
+                ay = fma(g.ty[tap], yv.y, ay);
+            }
+        }
+    }
+    return make_double2(ax, ay);
+}
+
 // block-wide sums of NV real values (results broadcast to every thread)
 template <typename R, int NV>
 __device__ __forceinline__ void block_sums(R (&v)[NV], R* scratch) {
@@ -87,6 +122,7 @@ __global__ void __launch_bounds__(512) k_bicgstab(BicgArgs a, void* scratch, int
     typedef typename Cx<R>::T C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ R red[6 * 32];
+    __shared__ double redd[32];
     const int N = a.g.N;
     C* base = use_smem ? reinterpret_cast<C*>(smem_raw)
                        : reinterpret_cast<C*>(scratch) + (long)blockIdx.x * 6 * N;
@@ -94,9 +130,14 @@ __global__ void __launch_bounds__(512) k_bicgstab(BicgArgs a, void* scratch, int
     C* bx = reinterpret_cast<C*>(a.X) + (long)blockIdx.x * N;   // right-hand side in, solution out
     const C mu = reinterpret_cast<const C*>(a.mu_dT)[blockIdx.x];
     const C zero = cmake((R)0, (R)0);
+    // FP64 reliable updates (complex64 solves with an FP64 accumulator)
+    const bool rel = sizeof(R) == 4 && a.x64 != nullptr && a.mu64 != nullptr;
+    double2* x64 = rel ? a.x64 + (long)blockIdx.x * N : nullptr;
+    const double2 mu64 = rel ? a.mu64[blockIdx.x] : make_double2(0.0, 0.0);
 
     // x0 = 0, r = r0 = b, p = v = 0
     R nb[1] = {(R)0};
+    double nb64[1] = {0.0};
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
         const C b = bx[i];
         V.x[i] = zero;
@@ -105,10 +146,54 @@ __global__ void __launch_bounds__(512) k_bicgstab(BicgArgs a, void* scratch, int
         V.p[i] = zero;
         V.v[i] = zero;
         nb[0] += b.x * b.x + b.y * b.y;
+        if (rel) {
+            x64[i] = make_double2(0.0, 0.0);
+            nb64[0] += (double)b.x * (double)b.x + (double)b.y * (double)b.y;
+        }
     }
     block_sums<R, 1>(nb, red);
+    if (rel) block_sums<double, 1>(nb64, redd);
     const R bnorm2 = nb[0];
     const R tol2 = (R)(a.tau * a.tau) * bnorm2;
+    const double tol2_64 = a.tau * a.tau * nb64[0];
+    R rmax2 = bnorm2;   // largest recursive |r|^2 since the last reliable update
+    // Reliable update: x64 += x, x = 0, r = b - (I - mu A) x64 in FP64 (kept
+    // in the working precision).  Returns |r|^2 in FP64; rn2 and rho_out get
+    // |r|^2 and <r0, r> in the working precision.
+    auto refresh = [&](R& rn2, C& rho_out) -> double {
+        __syncthreads();
+        for (int i = threadIdx.x; i < N; i += blockDim.x) {
+            const C xi = V.x[i];
+            double2 xd = x64[i];
+            xd.x += (double)xi.x;
+            xd.y += (double)xi.y;
+            x64[i] = xd;
+            V.x[i] = zero;
+        }
+        __syncthreads();
+        double d[1] = {0.0};
+        R f[3] = {(R)0, (R)0, (R)0};
+        for (int i = threadIdx.x; i < N; i += blockDim.x) {
+            const double2 Ax = stencil_fp64(a.g, x64, i);
+            const double2 xd = x64[i];
+            const C b = bx[i];
+            // r = b - x + mu A x
+            const double rx = (double)b.x - xd.x + (mu64.x * Ax.x - mu64.y * Ax.y);
+            const double ry = (double)b.y - xd.y + (mu64.x * Ax.y + mu64.y * Ax.x);
+            d[0] += rx * rx + ry * ry;
+            const C rf = cmake((R)rx, (R)ry);
+            V.r[i] = rf;
+            const C c = cmulc(rf, V.r0[i]);
+            f[0] += c.x;
+            f[1] += c.y;
+            f[2] += rf.x * rf.x + rf.y * rf.y;
+        }
+        block_sums<double, 1>(d, redd);
+        block_sums<R, 3>(f, red);
+        rn2 = f[2];
+        rho_out = cmake(f[0], f[1]);
+        return d[0];
+    };
     // |<r0, w>| below this fraction of |r0| |w| counts as a breakdown of the
     // bi-orthogonality and restarts the iteration with r0 = r
     const R brk = sizeof(R) == 8 ? (R)1e-12 : (R)1e-6;
@@ -172,8 +257,24 @@ __global__ void __launch_bounds__(512) k_bicgstab(BicgArgs a, void* scratch, int
         block_sums<R, 4>(d2, red);
         if (d2[3] <= tol2 || !(d2[2] > (R)0)) {   // converged on s (or t = 0): x += alpha p
             for (int i = threadIdx.x; i < N; i += blockDim.x) V.x[i] = cadd(V.x[i], cmul(alpha, V.p[i]));
-            status = d2[3] <= tol2 ? 1 : -1;
-            break;
+            if (!rel) {
+                status = d2[3] <= tol2 ? 1 : -1;
+                break;
+            }
+            // decide on the true residual; if it is above tau, restart from it
+            R rn2;
+            C rh;
+            const double t2 = refresh(rn2, rh);
+            if (t2 <= tol2_64) { status = 1; break; }
+            if (!(t2 == t2) || !(rn2 > (R)0)) { status = -1; break; }
+            if (++restarts > 64) { status = -1; break; }
+            for (int i = threadIdx.x; i < N; i += blockDim.x) V.r0[i] = V.r[i];
+            r0n2 = rn2;
+            rho = cmake(rn2, (R)0);
+            beta = cmake((R)0, (R)0);
+            rmax2 = rn2;
+            __syncthreads();
+            continue;
         }
         omega = cscale(cmake(d2[0], d2[1]), (R)1 / d2[2]);
         // x += alpha p + omega s;  r = s - omega t
@@ -188,7 +289,27 @@ __global__ void __launch_bounds__(512) k_bicgstab(BicgArgs a, void* scratch, int
             d3[2] += rn.x * rn.x + rn.y * rn.y;
         }
         block_sums<R, 3>(d3, red);
-        if (d3[2] <= tol2) { status = 1; break; }
+        if (rel) {
+            rmax2 = d3[2] > rmax2 ? d3[2] : rmax2;
+            if (d3[2] <= tol2 || d3[2] < (R)0.01 * rmax2) {
+                R rn2;
+                C rh;
+                const double t2 = refresh(rn2, rh);
+                if (t2 <= tol2_64) { status = 1; break; }
+                if (!(t2 == t2)) { status = -1; break; }
+                d3[0] = rh.x;
+                d3[1] = rh.y;
+                d3[2] = rn2;
+                rmax2 = rn2;
+                // progress is measured on true residuals from here on (the
+                // recursive one may have drifted below what is attainable)
+                best = rn2;
+                since_best = 0;
+            }
+        } else if (d3[2] <= tol2) {
+            status = 1;
+            break;
+        }
         if (!(d3[2] == d3[2])) { status = -1; break; }   // NaN
         if (d3[2] < (R)0.99 * best) {
             best = d3[2];
@@ -219,7 +340,15 @@ __global__ void __launch_bounds__(512) k_bicgstab(BicgArgs a, void* scratch, int
         rho = rho_new;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < N; i += blockDim.x) bx[i] = V.x[i];
+    if (rel) {
+        for (int i = threadIdx.x; i < N; i += blockDim.x) {
+            const C xi = V.x[i];
+            const double2 xd = x64[i];
+            bx[i] = cmake((R)(xd.x + (double)xi.x), (R)(xd.y + (double)xi.y));
+        }
+    } else {
+        for (int i = threadIdx.x; i < N; i += blockDim.x) bx[i] = V.x[i];
+    }
     // converged: it; stagnated: it + 2000000; iteration cap: it + 1000000; breakdown: -it
     if (threadIdx.x == 0)
         a.iters[blockIdx.x] = status < 0 ? -it : (status == 1 ? it : (status == 2 ? it + 2000000 : it + 1000000));

@@ -451,3 +451,31 @@ cudaError_t launch_w_minus(const double* u0, const double* b, const double* Cu, 
 }
 
 }  // namespace ac
+
+namespace ac {
+
+// FP64 FMA throughput probe: 8 independent chains of FMAs per thread whose
+// operands are all registers (a and b are loaded from memory, not taken
+// from the constant bank, which would slow the FMAs).
+__global__ void __launch_bounds__(256) k_dfma_rate(const double* __restrict__ ab, int rounds,
+                                                    double* __restrict__ sink) {
+    const double a = ab[0], b = ab[1];
+    double x[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = (double)(threadIdx.x + k) * 1e-3;
+    for (int r = 0; r < rounds; ++r) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) x[k] = fma(x[k], a, b);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += x[k];
+    if (s == ab[2]) sink[blockIdx.x] = s;   // ab[2] is never reached: keeps the chains live
+}
+
+cudaError_t launch_dfma_rate(const double* ab, int rounds, double* sink, int grid, cudaStream_t st) {
+    k_dfma_rate<<<grid, 256, 0, st>>>(ab, rounds, sink);
+    return cudaGetLastError();
+}
+
+}  // namespace ac

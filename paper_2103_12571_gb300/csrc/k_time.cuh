@@ -20,6 +20,7 @@
 #include "common.cuh"
 #include "fft.cuh"
 #include "kernels.h"
+#include "norm2.cuh"
 
 namespace ac {
 
@@ -139,7 +140,7 @@ template <typename R, int MM, int RAD, int DIM, bool GEN>
 __global__ void __launch_bounds__(256) k_fwd(FwdArgs a) {
     typedef typename Cx<R>::T C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ float red[32];
+    __shared__ double red[32];
     R* Zr = reinterpret_cast<R*>(smem_raw);
     C* Z = reinterpret_cast<C*>(smem_raw);
     const int P = a.P, HP = P >> 1;
@@ -184,7 +185,8 @@ __global__ void __launch_bounds__(256) k_fwd(FwdArgs a) {
             }
         }
     }
-    float sq = 0.f;
+    // sum of (r / w_scale)^2 * 2^40 as a float pair (FP32 and integer pipes)
+    F2Acc sq{0.f, 0.f};
 #ifndef AC_FWD_LUNROLL
 #define AC_FWD_LUNROLL 1
 #endif
@@ -201,14 +203,16 @@ __global__ void __launch_bounds__(256) k_fwd(FwdArgs a) {
         for (int u = 0; u < AC_FWD_LUNROLL; ++u) {
             const int l = l0 + u * lstep;
             if (l >= L) break;
-            const float isw = a.inv_s_w[l];
+            const float2 wv = a.wnorm[l];
 #pragma unroll
             for (int m = 0; m < MM; ++m) {
                 R v = (R)0;
                 if (n < N) {
-                    v = to_real<R>(r[u][m]);
-                    const float rf = (sizeof(R) == 4 ? (float)v : d2f_int(r[u][m])) * isw;
-                    sq = fmaf(rf, rf, sq);
+                    float hi, lo;
+                    split_d2f(r[u][m], hi, lo);
+                    if constexpr (sizeof(R) == 4) v = hi;   // hi is r rounded to nearest float
+                    else v = r[u][m];
+                    f2_add_sq(sq, hi, lo, wv.x, wv.y);
                 }
                 Zr[((long)l * MM + m) * P + p] = v;
             }
@@ -250,7 +254,7 @@ __global__ void __launch_bounds__(256) k_fwd(FwdArgs a) {
             else if (nn < N) dst[0] = xa;
         }
     }
-    const float tot = block_sum(sq, red);
+    const double tot = block_sum_f2(sq, red);
     if (threadIdx.x == 0) a.part[blockIdx.x] = tot;
 }
 
@@ -258,7 +262,7 @@ template <typename R, int MM>
 __global__ void __launch_bounds__(256) k_upd(UpdArgs a) {
     typedef typename Cx<R>::T C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ float red[32];
+    __shared__ unsigned long long red[32];
     C* Z = reinterpret_cast<C*>(smem_raw);
     const int P = a.P, HP = P >> 1;
     const int logP = 31 - __clz(P), logHP = logP - 1;
@@ -300,7 +304,11 @@ __global__ void __launch_bounds__(256) k_upd(UpdArgs a) {
 
     fft_inv<C, MM, true>(Z, a.logL, logHP, MM * HP, 1, HP, reinterpret_cast<const C*>(a.tw));
 
-    float emax = 0.f;
+    // max over the last time block, in FP64 as bit patterns (integer pipe):
+    // of |z| (correction form: |e| = sv |z| with one sv for the whole block),
+    // or of |u_new - u_old| (overwrite form)
+    const unsigned long long kAbs = 0x7FFFFFFFFFFFFFFFull;
+    unsigned long long emax = 0ull;
     const bool pairs = (N & 1) == 0 && a.out_aligned16;
 #pragma unroll 4
     for (int idx = threadIdx.x; idx < L * MM * HP; idx += blockDim.x) {
@@ -313,9 +321,9 @@ __global__ void __launch_bounds__(256) k_upd(UpdArgs a) {
         double* o = a.out + ((long)l * MM + m) * N + nn;
         const double za = to_double(z.x), zb = to_double(z.y);
         if (l == L - 1 && !a.diff_last) {
-            const float zx = sizeof(R) == 4 ? (float)z.x : d2f_int((double)z.x);
-            const float zy = sizeof(R) == 4 ? (float)z.y : d2f_int((double)z.y);
-            emax = fmaxf(emax, fmaxf(fabsf(zx), fabsf(zy)) * d2f_int(sv));
+            const unsigned long long ba = bits_of(za) & kAbs, bb = bits_of(zb) & kAbs;
+            emax = ba > emax ? ba : emax;
+            emax = bb > emax ? bb : emax;
         }
         double prev0 = 0.0, prev1 = 0.0;
         if (a.diff_last && l == L - 1) {
@@ -332,11 +340,17 @@ __global__ void __launch_bounds__(256) k_upd(UpdArgs a) {
             if (nn + 1 < N) o[1] = fma(sv, zb, a.accumulate ? o[1] : 0.0);
         }
         if (a.diff_last && l == L - 1) {   // overwrite mode: |u_L^{k+1} - u_L^k| (old values read above)
-            emax = fmaxf(emax, fmaxf(d2f_int(fabs(prev0 - sv * za)), d2f_int(fabs(prev1 - sv * zb))));
+            const unsigned long long ba = nn < N ? bits_of(prev0 - fma(sv, za, 0.0)) & kAbs : 0ull;
+            const unsigned long long bb = nn + 1 < N ? bits_of(prev1 - fma(sv, zb, 0.0)) & kAbs : 0ull;
+            emax = ba > emax ? ba : emax;
+            emax = bb > emax ? bb : emax;
         }
     }
-    const float tot = block_max(emax, red);
-    if (threadIdx.x == 0) a.part[blockIdx.x] = tot;
+    const unsigned long long mx = block_max_bits(emax, red);
+    if (threadIdx.x == 0) {
+        const double v = __longlong_as_double((long long)mx);
+        a.part[blockIdx.x] = a.diff_last ? v : v * a.sinv[L - 1];
+    }
 }
 
 template <typename R, int MM, int RAD, int DIM, bool GEN>

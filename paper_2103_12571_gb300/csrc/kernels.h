@@ -32,11 +32,11 @@ struct FwdArgs {
     double alpha;                // alpha of the recompute form
     const double* qs;            // [L][M][M] s_l * dT * Q (Q^T if transposed)
     const double* s;             // [L] s_l = alpha^{l/L}
-    const float* inv_s_w;        // [L] 1 / (s_l * w_scale) for the residual norm
+    const float2* wnorm;         // [L] 2^20 / (s_l * w_scale) as a float pair (hi, lo), for the residual norm
     const void* tw;              // L/2 twiddles exp(-2 pi i k / L), complex of the kernel type
     const void* Sinv;            // [F][M][M] complex of the kernel type
     void* X;                     // [F][M][N] complex of the kernel type
-    float* part;                 // [gridDim.x] partial sums of (r / w_scale)^2
+    double* part;                // [gridDim.x] partial sums of (2^20 r / w_scale)^2
 };
 
 // Node back-mixing + inverse time FFT + un-scaling + update (eqs. (d3),
@@ -51,7 +51,7 @@ struct UpdArgs {
     int accumulate;              // 1: out += e, 0: out = e
     int out_aligned16;           // out is 16-byte aligned (set by launch_upd): double2 access allowed
     int diff_last;               // with accumulate = 0: part = max |out_new - out_old| over the last time block
-    float* part;                 // [gridDim.x] max |e| over the last time block
+    double* part;                // [gridDim.x] max |e| (or |u_new - u_old|) over the last time block
 };
 
 // Spatial solves of eq. (d2) on the F*M planes X[f][m][:].
@@ -74,6 +74,9 @@ struct BicgArgs {
     void* X;                     // in: right-hand sides, out: solutions
     const void* mu_dT;
     int* iters;                  // [planes] iterations used (negative on breakdown)
+    // complex64 solves with FP64 reliable updates (both null otherwise)
+    const double2* mu64;         // [planes] dT mu in FP64
+    double2* x64;                // [planes][N] FP64 solution accumulators
 };
 
 struct GmresArgs {

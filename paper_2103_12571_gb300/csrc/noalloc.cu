@@ -94,34 +94,18 @@ template <typename R>
 int run(const ac_problem* prob, int M, int L, double dT, double alpha, const double* r, double* e,
         cudaStream_t st) {
     const bool dbl = sizeof(R) == 8;
+    const int precision = dbl ? AC_C128 : AC_C64;
     const size_t cs = 2 * sizeof(R);
     const int nx = prob->nx, ny = prob->dim == 2 ? prob->ny : 1;
     const long long N = (long long)nx * ny;
     const int F = L / 2 + 1;
 
-    // spatial path and time tile, chosen as ac_setup chooses them
-    int path, rpb = 1, W = 1;
-    if (prob->dim == 1) {
-        if ((size_t)nx * cs > 160 * 1024) return nfail(AC_ERR_INVALID_ARG, "1D grid too large");
-        path = 0;
-    } else if ((size_t)nx * ny * cs <= 160 * 1024) {
-        path = 1;
-    } else {
-        path = 2;
-        rpb = (int)(32768 / ((size_t)nx * cs));
-        if (rpb < 1) rpb = 1;
-        while (rpb & (rpb - 1)) rpb &= rpb - 1;
-        if (rpb > ny) rpb = ny;
-        W = (int)(128 / cs);
-        if (W > nx) W = nx;
-        if ((size_t)nx * cs > 160 * 1024 || (size_t)ny * W * cs > 160 * 1024)
-            return nfail(AC_ERR_INVALID_ARG, "2D grid too large");
-    }
-    int P = 256;
-    while (P > 2 && (size_t)L * M * P * sizeof(R) > 50 * 1024) P >>= 1;
-    while (P > 16 && (N + P - 1) / P < 2 * 152) P >>= 1;
-    if ((size_t)L * M * P * sizeof(R) > 200 * 1024) return nfail(AC_ERR_INVALID_ARG, "L*M too large");
-    const int grid = (int)((N + P - 1) / P);
+    ac::Stencil sten;
+    if (!ac::problem_stencil(*prob, &sten)) return nfail(AC_ERR_INVALID_ARG, "unsupported stencil");
+    // spatial path and kernel tiles: the ones ac_setup chooses for this problem
+    ac::PlanShape sh;
+    if (const char* why = ac::plan_shape(*prob, M, L, precision, AC_INNER_FFT, sten.rad, &sh))
+        return nfail(AC_ERR_INVALID_ARG, why);
 
     // carve the scratch array
     size_t off = 0;
@@ -134,10 +118,10 @@ int run(const ac_problem* prob, int M, int L, double dT, double alpha, const dou
     const size_t otwL = take((size_t)L * cs), otwx = take((size_t)nx * cs), otwy = take((size_t)ny * cs);
     const size_t osx = take((size_t)nx * cs), osy = take((size_t)ny * cs);
     const size_t oqs = take(sizeof(double) * (size_t)L * M * M), os = take(sizeof(double) * L);
-    const size_t oisw = take(sizeof(float) * L), osinv = take(sizeof(double) * L);
+    const size_t own = take(2 * sizeof(float) * L), osinv = take(sizeof(double) * L);
     const size_t oSinv = take((size_t)F * M * M * cs), oP = take((size_t)F * M * M * cs);
     const size_t omu = take((size_t)F * M * cs);
-    const size_t opf = take(sizeof(float) * grid), opu = take(sizeof(float) * grid);
+    const size_t opf = take(sizeof(double) * sh.grid), opu = take(sizeof(double) * sh.grid_upd);
     if (off > kScratchBytes) {
         char msg[256];
         std::snprintf(msg, sizeof(msg),
@@ -150,52 +134,37 @@ int run(const ac_problem* prob, int M, int L, double dT, double alpha, const dou
     int rc = scratch_address(&base);
     if (rc) return rc;
 
-    // host tables (Radau IIA data, stencil, twiddles, alpha-dependent tables)
+    // host tables: Radau IIA data, twiddles, stencil symbols and the
+    // alpha-dependent tables, from the same routines as ac_setup
     double t[8], Q[64];
     ac::radau_nodes(M, t);
     ac::collocation_matrix(M, t, Q);
-    ac::Stencil sten;
-    if (!ac::problem_stencil(*prob, &sten)) return nfail(AC_ERR_INVALID_ARG, "unsupported stencil");
-    const double* tx = sten.tx;
-    const double* ty = sten.ty;
-    auto tw = [](int n) {
-        std::vector<ac::cd> v(n);
-        for (int k = 0; k < n; ++k) v[k] = std::exp(ac::cd(0.0, -2.0 * M_PI * k / n));
-        return v;
-    };
-    std::vector<ac::cd> sx(nx), sy(ny, ac::cd(0.0));
-    ac::axis_symbol(nx, tx, sx.data());
-    if (prob->dim == 2) ac::axis_symbol(ny, ty, sy.data());
-    std::vector<double> qs((size_t)L * M * M), s(L), sinv(L);
-    std::vector<float> isw(L);
-    for (int l = 0; l < L; ++l) {
-        s[l] = l == 0 ? 1.0 : std::pow(alpha, (double)l / L);
-        sinv[l] = (l == 0 ? 1.0 : std::pow(alpha, -(double)l / L)) / L;
-        isw[l] = (float)(1.0 / s[l]);
-        for (int m = 0; m < M; ++m)
-            for (int j = 0; j < M; ++j) qs[((size_t)l * M + m) * M + j] = s[l] * dT * Q[m * M + j];
-    }
-    std::vector<ac::cd> mu((size_t)F * M), Sinv((size_t)F * M * M), Pm((size_t)F * M * M);
-    double worst = ac::freq_tables(M, L, alpha, false, Q, t, mu.data(), Sinv.data(), Pm.data(), nullptr);
-    if (worst < 0 || worst > 1e10) return nfail(AC_ERR_NOT_DIAGONALIZABLE, "Q G_l^{-1} not diagonalisable");
-    for (auto& v : mu) v *= dT;
+    std::vector<ac::cd> twL, twx, twy, sx(nx), sy(ny, ac::cd(0.0));
+    ac::twiddles(L, twL);
+    ac::twiddles(nx, twx);
+    ac::twiddles(ny, twy);
+    ac::axis_symbol(nx, sten.tx, sx.data());
+    if (prob->dim == 2) ac::axis_symbol(ny, sten.ty, sy.data());
+    ac::AlphaTables T;
+    if (!ac::alpha_tables(M, L, dT, Q, t, alpha, false, 1.0, &T))
+        return nfail(AC_ERR_NOT_DIAGONALIZABLE, "Q G_l^{-1} not diagonalisable");
 
     cudaError_t ce = cudaSuccess;
     auto chk = [&ce](cudaError_t x) {
         if (ce == cudaSuccess) ce = x;
     };
-    chk(put_c(base + otwL, tw(L), dbl, st));
-    chk(put_c(base + otwx, tw(nx), dbl, st));
-    chk(put_c(base + otwy, tw(ny), dbl, st));
+    chk(put_c(base + otwL, twL, dbl, st));
+    chk(put_c(base + otwx, twx, dbl, st));
+    chk(put_c(base + otwy, twy, dbl, st));
     chk(put_c(base + osx, sx, dbl, st));
     chk(put_c(base + osy, sy, dbl, st));
-    chk(cudaMemcpyAsync(base + oqs, qs.data(), qs.size() * sizeof(double), cudaMemcpyHostToDevice, st));
-    chk(cudaMemcpyAsync(base + os, s.data(), s.size() * sizeof(double), cudaMemcpyHostToDevice, st));
-    chk(cudaMemcpyAsync(base + oisw, isw.data(), isw.size() * sizeof(float), cudaMemcpyHostToDevice, st));
-    chk(cudaMemcpyAsync(base + osinv, sinv.data(), sinv.size() * sizeof(double), cudaMemcpyHostToDevice, st));
-    chk(put_c(base + oSinv, Sinv, dbl, st));
-    chk(put_c(base + oP, Pm, dbl, st));
-    chk(put_c(base + omu, mu, dbl, st));
+    chk(cudaMemcpyAsync(base + oqs, T.qs.data(), T.qs.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    chk(cudaMemcpyAsync(base + os, T.s.data(), T.s.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    chk(cudaMemcpyAsync(base + own, T.wnorm.data(), T.wnorm.size() * sizeof(float), cudaMemcpyHostToDevice, st));
+    chk(cudaMemcpyAsync(base + osinv, T.sinv.data(), T.sinv.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    chk(put_c(base + oSinv, T.Sinv, dbl, st));
+    chk(put_c(base + oP, T.P, dbl, st));
+    chk(put_c(base + omu, T.mu_dT, dbl, st));
     if (ce != cudaSuccess) return nfail(AC_ERR_CUDA, cudaGetErrorString(ce));
 
     ac::Grid g;
@@ -205,10 +174,10 @@ int run(const ac_problem* prob, int M, int L, double dT, double alpha, const dou
     g.N = (int)N;
     g.rad = sten.rad;
     for (int i = 0; i < 7; ++i) {
-        g.tx[i] = tx[i];
-        g.ty[i] = ty[i];
+        g.tx[i] = sten.tx[i];
+        g.ty[i] = sten.ty[i];
     }
-    g.c0 = tx[3] + ty[3];
+    g.c0 = sten.tx[3] + sten.ty[3];
 
     ac::FwdArgs fa{};
     fa.g = g;
@@ -216,7 +185,7 @@ int run(const ac_problem* prob, int M, int L, double dT, double alpha, const dou
     fa.L = L;
     fa.logL = log2i(L);
     fa.F = F;
-    fa.P = P;
+    fa.P = sh.P;
     fa.u = nullptr;
     fa.u0 = nullptr;
     fa.b = r;
@@ -224,13 +193,12 @@ int run(const ac_problem* prob, int M, int L, double dT, double alpha, const dou
     fa.transposed = 0;
     fa.qs = reinterpret_cast<const double*>(base + oqs);
     fa.s = reinterpret_cast<const double*>(base + os);
-    fa.inv_s_w = reinterpret_cast<const float*>(base + oisw);
+    fa.wnorm = reinterpret_cast<const float2*>(base + own);
     fa.tw = base + otwL;
     fa.Sinv = base + oSinv;
     fa.X = base + oX;
-    fa.part = reinterpret_cast<float*>(base + opf);
-    const size_t smem = (size_t)L * M * P * sizeof(R);
-    chk(ac::launch_fwd<R>(fa, grid, smem, st));
+    fa.part = reinterpret_cast<double*>(base + opf);
+    chk(ac::launch_fwd<R>(fa, sh.grid, (size_t)L * M * sh.P * sizeof(R), st));
 
     ac::SpaceArgs sa{};
     sa.nx = nx;
@@ -245,10 +213,10 @@ int run(const ac_problem* prob, int M, int L, double dT, double alpha, const dou
     sa.sig_y = base + osy;
     sa.tw_x = base + otwx;
     sa.tw_y = base + otwy;
-    sa.rows_per_block = rpb;
-    sa.cols_per_block = W;
-    if (path == 0) chk(ac::launch_space_1d<R>(sa, st));
-    else if (path == 1) chk(ac::launch_space_2d_small<R>(sa, st));
+    sa.rows_per_block = sh.rows_per_block;
+    sa.cols_per_block = sh.cols_per_block;
+    if (sh.spatial_path == 0) chk(ac::launch_space_1d<R>(sa, st));
+    else if (sh.spatial_path == 1) chk(ac::launch_space_2d_small<R>(sa, st));
     else {
         chk(ac::launch_space_rows<R>(sa, 0, st));
         chk(ac::launch_space_cols<R>(sa, st));
@@ -261,15 +229,15 @@ int run(const ac_problem* prob, int M, int L, double dT, double alpha, const dou
     ua.L = L;
     ua.logL = log2i(L);
     ua.F = F;
-    ua.P = P;
+    ua.P = sh.P_upd;
     ua.X = base + oX;
     ua.Pm = base + oP;
     ua.tw = base + otwL;
     ua.sinv = reinterpret_cast<const double*>(base + osinv);
     ua.out = e;
     ua.accumulate = 0;
-    ua.part = reinterpret_cast<float*>(base + opu);
-    chk(ac::launch_upd<R>(ua, grid, smem, st));
+    ua.part = reinterpret_cast<double*>(base + opu);
+    chk(ac::launch_upd<R>(ua, sh.grid_upd, (size_t)L * M * sh.P * sizeof(R), st));
     if (ce != cudaSuccess) return nfail(AC_ERR_CUDA, cudaGetErrorString(ce));
     return AC_OK;
 }

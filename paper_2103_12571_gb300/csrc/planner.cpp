@@ -412,6 +412,94 @@ void axis_symbol(int n, const double taps[7], cd* sigma) {
     }
 }
 
+void twiddles(int n, std::vector<cd>& tw) {
+    tw.resize(n);
+    for (int k = 0; k < n; ++k) tw[k] = std::exp(cd(0.0, -2.0 * M_PI * k / n));
+}
+
+static bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+const char* plan_shape(const ac_problem& prob, int M, int L, int precision, int inner, int rad, PlanShape* o) {
+    const int nx = prob.nx, ny = prob.dim == 2 ? prob.ny : 1;
+    const long long N = (long long)nx * ny;
+    const size_t cs = precision == AC_C128 ? 16 : 8;   // bytes per complex of the transform
+    *o = PlanShape{};
+    o->rows_per_block = 1;
+    o->cols_per_block = 1;
+    if (inner == AC_INNER_FFT) {
+        if (!is_pow2(nx) || !is_pow2(ny)) return "the FFT inner solver needs power-of-two grid sizes";
+        if (prob.dim == 1) {
+            if ((size_t)nx * cs > 160 * 1024) return "1D grid too large for the one-CTA FFT solve";
+            o->spatial_path = 0;
+        } else if ((size_t)nx * ny * cs <= 160 * 1024) {
+            o->spatial_path = 1;
+        } else {
+            o->spatial_path = 2;
+            int rpb = (int)(32768 / ((size_t)nx * cs));
+            if (rpb < 1) rpb = 1;
+            while (rpb & (rpb - 1)) rpb &= rpb - 1;
+            o->rows_per_block = rpb < ny ? rpb : ny;
+            int W = (int)(128 / cs);
+            if (W > nx) W = nx;
+            o->cols_per_block = W;
+            if ((size_t)nx * cs > 160 * 1024 || (size_t)ny * W * cs > 160 * 1024)
+                return "2D grid too large for the three-pass FFT solve";
+        }
+    } else {
+        o->spatial_path = inner == AC_INNER_GMRES ? 4 : 3;
+        if (nx < 2 * rad + 1 || (prob.dim == 2 && ny < 2 * rad + 1)) return "grid smaller than the stencil";
+    }
+    // tile of the time kernels: P points, L*M*P reals of shared memory
+    const size_t rsz = cs / 2;
+    int P = 256;
+    while (P > 2 && (size_t)L * M * P * rsz > 50 * 1024) P >>= 1;
+    while (P > 16 && (N + P - 1) / P < 2 * 152) P >>= 1;
+    if ((size_t)L * M * P * rsz > 200 * 1024) return "L*M too large for the shared-memory time transform";
+    // The update kernel is latency-bound: smaller tiles while its grid has
+    // fewer than three CTAs per SM (1D advection, 4096 points: 16 -> 8 points,
+    // 18% faster); on larger grids halving the tile measured slower.
+    int Pu = P;
+    while (Pu > 8 && (N + Pu - 1) / Pu < 3 * 152) Pu >>= 1;
+    // The residual kernel is FP64-bound.  In complex64 plans smaller tiles
+    // (more CTAs) let its FP64 phase overlap better with the transform phases
+    // of other CTAs: a quarter of tiles of 64 points and more (2D heat 256^2:
+    // 64 -> 16 points, 6% faster than 64), half of tiles of 16 to 32 points
+    // (1D advection: 16 -> 8, 3%); tiles under 8 points and complex128 plans
+    // measured slower.
+    o->P = precision != AC_C64 ? P : (P >= 64 ? P / 4 : (P >= 16 ? P / 2 : P));
+    o->grid = (int)((N + o->P - 1) / o->P);
+    o->P_upd = Pu;
+    o->grid_upd = (int)((N + Pu - 1) / Pu);
+    return nullptr;
+}
+
+bool alpha_tables(int M, int L, double dT, const double* Q, const double* t, double alpha, bool transposed,
+                  double wscale, AlphaTables* o) {
+    const int F = L / 2 + 1;
+    o->qs.assign((size_t)L * M * M, 0.0);
+    o->s.assign(L, 0.0);
+    o->sinv.assign(L, 0.0);
+    o->wnorm.assign(2 * (size_t)L, 0.f);
+    for (int l = 0; l < L; ++l) {
+        o->s[l] = (l == 0) ? 1.0 : std::pow(alpha, (double)l / L);
+        o->sinv[l] = ((l == 0) ? 1.0 : std::pow(alpha, -(double)l / L)) / L;
+        const double w = 1048576.0 / (o->s[l] * wscale);   // 2^20: the kernels' norm prescale
+        const float wh = (float)w;
+        o->wnorm[2 * l] = wh;
+        o->wnorm[2 * l + 1] = (float)(w - (double)wh);
+        for (int m = 0; m < M; ++m)
+            for (int j = 0; j < M; ++j)
+                o->qs[((size_t)l * M + m) * M + j] = o->s[l] * dT * (transposed ? Q[j * M + m] : Q[m * M + j]);
+    }
+    o->mu_dT.assign((size_t)F * M, cd(0.0));
+    o->Sinv.assign((size_t)F * M * M, cd(0.0));
+    o->P.assign((size_t)F * M * M, cd(0.0));
+    o->worst_cond = freq_tables(M, L, alpha, transposed, Q, t, o->mu_dT.data(), o->Sinv.data(), o->P.data(), nullptr);
+    if (o->worst_cond < 0 || o->worst_cond > 1e10) return false;
+    for (auto& v : o->mu_dT) v *= dT;
+    return true;
+}
+
 }  // namespace ac
 
 // ------------------------------------------------------------- C ABI (host)

@@ -46,4 +46,39 @@ bool problem_stencil(const ac_problem& prob, Stencil* st);
 // Symbol sigma(k) = sum_o taps[o + 3] exp(2 pi i k o / n), k = 0..n-1.
 void axis_symbol(int n, const double taps[7], cd* sigma);
 
+// w_n^k = exp(-2 pi i k / n), k < n (the full circle: the mixed-radix FFT
+// stages index it with j * r).
+void twiddles(int n, std::vector<cd>& tw);
+
+// Launch shape of the solver for a problem: which spatial solve runs and
+// the tiles of the time and spatial kernels.  ac_setup and the
+// allocation-free preconditioner both take it from here, so that they run
+// the same launches.
+struct PlanShape {
+    int spatial_path;               // 0: 1D FFT, one CTA per plane; 1: 2D FFT, one CTA per plane;
+                                    // 2: 2D FFT in three passes; 3: BiCGStab; 4: GMRES
+    int rows_per_block, cols_per_block;   // three-pass tiles
+    int P, grid;                    // residual kernel: grid points per CTA, CTAs
+    int P_upd, grid_upd;            // update kernel: grid points per CTA, CTAs
+};
+// Null on success, else a message naming the unsupported size.  rad: the
+// stencil radius (Krylov paths need 2 rad + 1 points per axis).
+const char* plan_shape(const ac_problem& prob, int M, int L, int precision, int inner, int rad,
+                       PlanShape* out);
+
+// The alpha-dependent tables of one preconditioner (Lemma 1, eq. (QGL)):
+// per step l: s_l = alpha^{l/L}, qs_l = s_l dT Q (Q^T if transposed),
+// sinv_l = alpha^{-l/L} / L, the residual-norm weight 2^20 / (s_l w_scale)
+// as a float pair; per stored frequency f: dT mu_{f,m}, S_f^{-1} and
+// P_f = G_f^{-1} S_f.  Returns false (with worst_cond set) if some S_f is
+// ill-conditioned (cond > 1e10) or the eigen-decomposition failed.
+struct AlphaTables {
+    std::vector<double> qs, s, sinv;
+    std::vector<float> wnorm;       // 2 L floats: (hi, lo) per step
+    std::vector<cd> mu_dT, Sinv, P;
+    double worst_cond;
+};
+bool alpha_tables(int M, int L, double dT, const double* Q, const double* t, double alpha, bool transposed,
+                  double wscale, AlphaTables* out);
+
 }  // namespace ac
