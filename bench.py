@@ -396,8 +396,10 @@ def run_ours(args):
     flush = None if big else torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     # ---- headline: one FP64 Richardson iteration, inputs resident in HBM
-    plan = Plan(prob, precision="c128", alpha="paper", max_iter=60)
-    alpha = correction_alpha(L, "c128")
+    # (--mixed, for profiling captures only: the complex64 preconditioner)
+    hprec = "c64" if args.mixed else "c128"
+    plan = Plan(prob, precision=hprec, alpha="paper", max_iter=60)
+    alpha = correction_alpha(L, hprec)
     u = u0.repeat(L * M).reshape(L, M, N).contiguous()
     for _ in range(args.warmup):
         plan.richardson_step(alpha, u0, u)
@@ -429,10 +431,10 @@ def run_ours(args):
     ms = max_over_ranks(float(np.mean(step_ms)), world)
     value = job_value(D, ms, world)
     fp64_tflops = 2 * measure_fp64_fma_rate() / 1e12
-    counts64 = kernel_counts(prob, 16, taps)
-    ktab = kernel_table(prof, counts64, "c128", args.steps, fp64_tflops)
+    counts64 = kernel_counts(prob, 16 if hprec == "c128" else 8, taps)
+    ktab = kernel_table(prof, counts64, hprec, args.steps, fp64_tflops)
     dom = dominant_kernel(ktab)
-    roof = roofline(dom, single[dom], counts64, "c128", fp64_tflops)
+    roof = roofline(dom, ktab[dom], counts64, hprec, fp64_tflops)
     cfgd = workload_config(args.workload)
     if args.L:
         cfgd = dict(cfgd, L=L, T=prob["T"], DoF=D, workload=cfgd["workload"] + "_L%d" % L)
@@ -440,8 +442,8 @@ def run_ours(args):
     if args.no_extras:
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "ms_per_step": ms, "steps": args.steps,
-                              "warmup": args.warmup, "dtype": "f64", "config": cfgd, "kernels": ktab,
-                              "roofline": roof}))
+                              "warmup": args.warmup, "dtype": "f64" if hprec == "c128" else "f64+c64",
+                              "config": cfgd, "kernels": ktab, "roofline": roof}))
         return
 
     # ---- end to end through the public API with host buffers: every step
@@ -693,6 +695,8 @@ def main():
     ap.add_argument("--no-configs", action="store_true", help="skip the per-workload section")
     ap.add_argument("--no-extras", action="store_true",
                     help="only the timed steps (used for ncu captures): no e2e, time-to-tolerance or CPU legs")
+    ap.add_argument("--mixed", action="store_true",
+                    help="with --no-extras: time the mixed form's iteration instead (profiling captures)")
     ap.add_argument("--oracle-worker", type=int, default=0, help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.oracle_worker:
@@ -700,6 +704,8 @@ def main():
         return
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
+    if args.mixed and not args.no_extras:
+        ap.error("--mixed is a profiling switch: use it with --no-extras")
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -14,7 +14,8 @@
 //   since the last update (or meets tau) the update so far is added to it and
 //   the residual is replaced by b - (I - mu A) x computed in FP64.  The
 //   iteration continues with that residual, and convergence is decided on
-//   it, so complex64 solves reach tolerances below the FP32 floor.  The loop is
+//   it, so complex64 solves reach tolerances below the FP32 floor; a
+//   stagnated system restarts from its true residual (at most 8 times).  The loop is
 //   bounded by max_iter and stops early when the residual has not dropped
 //   below 0.99 of its best value for 256 iterations (stagnation at the
 //   precision floor).  A near-breakdown of the bi-orthogonality (|<r0, v>|
@@ -201,7 +202,7 @@ __global__ void __launch_bounds__(512) k_bicgstab(BicgArgs a, void* scratch, int
     R r0n2 = bnorm2;                       // |r0|^2
     C alpha = cmake((R)1, (R)0), omega = cmake((R)1, (R)0);
     C beta = cmake((R)0, (R)0);
-    int it = 0, status = 0, since_best = 0, restarts = 0;
+    int it = 0, status = 0, since_best = 0, restarts = 0, stag_restarts = 0;
     R best = bnorm2;
     if (bnorm2 == (R)0) status = 1;
     if (!(bnorm2 >= (R)0) || bnorm2 > (R)3e38) status = -1;   // non-finite right-hand side: reported, x = 0
@@ -315,6 +316,24 @@ __global__ void __launch_bounds__(512) k_bicgstab(BicgArgs a, void* scratch, int
             best = d3[2];
             since_best = 0;
         } else if (++since_best >= 256) {
+            if (rel && stag_restarts < 8) {
+                // restart from the FP64 true residual with a fresh shadow vector
+                ++stag_restarts;
+                R rn2;
+                C rh;
+                const double t2 = refresh(rn2, rh);
+                if (t2 <= tol2_64) { status = 1; break; }
+                if (!(t2 == t2) || !(rn2 > (R)0)) { status = -1; break; }
+                for (int i = threadIdx.x; i < N; i += blockDim.x) V.r0[i] = V.r[i];
+                r0n2 = rn2;
+                rho = cmake(rn2, (R)0);
+                beta = cmake((R)0, (R)0);
+                rmax2 = rn2;
+                best = rn2;
+                since_best = 0;
+                __syncthreads();
+                continue;
+            }
             status = 2;   // stagnated
             break;
         }

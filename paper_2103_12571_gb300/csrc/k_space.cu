@@ -5,31 +5,48 @@
 // Forward FFTs leave the spectrum in digit-reversed order and the inverse
 // FFTs take it back from there, so no reordering pass is needed: the
 // division only needs the true wavenumber of each slot (digitrev).
+//
+// Radix plans (template SB: stages of up to 2^SB points).  Complex64
+// transforms use radix 8 (register pressure).  Complex128 transforms run on
+// the FP64 pipe, where the instruction count per point is what counts: per
+// point and stage a radix-16 stage costs 14.25 FP64 instructions with
+// twiddles (10.5 without), radix 8 10.5 (7), radix 4 7 (4), radix 2 4 (2),
+// so lengths 2^6 and 2^9 take radix 8 (8*8*8: 28 per point for 512 points,
+// against 30.5 for 16*16*2) and the others radix 16.
 #include "common.cuh"
 #include "fft.cuh"
 #include "kernels.h"
 
 namespace ac {
 
-// v / (1 - mu * sig): multiply by conj(den) / |den|^2 with one reciprocal
-// (|den| >= 1 here whenever Re(mu sig) <= 0, so no scaling is needed)
-__device__ __forceinline__ float rcp_c64(float x) { return __frcp_rn(x); }
-__device__ __forceinline__ double rcp_c64(double x) { return 1.0 / x; }
+// Reciprocal of a positive double: a float seed (FP32 reciprocal, converted
+// on the integer pipe) and two Newton-Raphson steps y <- y + y (1 - x y),
+// each of which doubles the number of correct bits (24 -> 48 -> full FP64).
+// Valid for x in the normal float range, which the shifted symbols
+// |1 - mu sigma|^2 of the solver stay in.
+__device__ __forceinline__ double rcp_newton(double x, double one) {
+    double y = f2d_int(__frcp_rn(d2f_int(x)));
+    y = fma(y, fma(-x, y, one), y);
+    y = fma(y, fma(-x, y, one), y);
+    return y;
+}
+__device__ __forceinline__ float rcp_newton(float x, float) { return __frcp_rn(x); }
 
-template <typename C>
-__device__ __forceinline__ C shift_div(C v, C mu, C sig) {
-    C den = cmul(mu, sig);
-    den.x = (decltype(den.x))1 - den.x;
-    den.y = -den.y;
-    const auto inv = rcp_c64(den.x * den.x + den.y * den.y);
+// v / (1 - m) with m = mu sigma: multiply by conj(1 - m) / |1 - m|^2
+// (|1 - m| >= 1 whenever Re(mu sigma) <= 0; in any case far from 0 here).
+template <typename C, typename R>
+__device__ __forceinline__ C div_one_minus(C v, C m, R one) {
+    C den;
+    den.x = one - m.x;
+    den.y = -m.y;
+    const R inv = rcp_newton(fma(den.x, den.x, den.y * den.y), one);
     return cscale(cmulc(v, den), inv);
 }
 
 // One CTA per 1D plane held in shared memory.
-template <typename R>
+template <typename R, int SB>
 __global__ void __launch_bounds__(512) k_space_1d(SpaceArgs a) {
     typedef typename Cx<R>::T C;
-    constexpr int SB = sizeof(R) == 8 ? 4 : 3;   // radix 16 in FP64, radix 8 in FP32 (register pressure)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* d = reinterpret_cast<C*>(smem_raw);
     const int n = a.nx, logn = a.lognx;
@@ -37,10 +54,14 @@ __global__ void __launch_bounds__(512) k_space_1d(SpaceArgs a) {
     for (int i = threadIdx.x; i < n; i += blockDim.x) d[i] = x[i];
     __syncthreads();
     const C* tw = reinterpret_cast<const C*>(a.tw_x);
+    const R one = tw[0].x;
     fft_fwd<C, 1, false, SB>(d, logn, 0, 1, 0, 0, tw);
     const C mu = reinterpret_cast<const C*>(a.mu_dT)[blockIdx.x];
     const C* sig = reinterpret_cast<const C*>(a.sig_x);
-    for (int i = threadIdx.x; i < n; i += blockDim.x) d[digitrev<SB>(i, logn)] = shift_div(d[digitrev<SB>(i, logn)], mu, sig[i]);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int s = digitrev<SB>(i, logn);
+        d[s] = div_one_minus(d[s], cmul(mu, sig[i]), one);
+    }
     __syncthreads();
     fft_inv<C, 1, false, SB>(d, logn, 0, 1, 0, 0, tw);
     const R sc = (R)1 / (R)n;
@@ -49,10 +70,9 @@ __global__ void __launch_bounds__(512) k_space_1d(SpaceArgs a) {
 
 // One CTA per 2D plane held in shared memory (row FFTs, column FFTs, divide,
 // inverse column and row FFTs).
-template <typename R>
+template <typename R, int SBX, int SBY>
 __global__ void __launch_bounds__(512) k_space_2d_small(SpaceArgs a) {
     typedef typename Cx<R>::T C;
-    constexpr int SB = sizeof(R) == 8 ? 4 : 3;   // radix 16 in FP64, radix 8 in FP32 (register pressure)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* d = reinterpret_cast<C*>(smem_raw);
     const int nx = a.nx, ny = a.ny, lx = a.lognx, ly = a.logny;
@@ -62,29 +82,29 @@ __global__ void __launch_bounds__(512) k_space_2d_small(SpaceArgs a) {
     __syncthreads();
     const C* twx = reinterpret_cast<const C*>(a.tw_x);
     const C* twy = reinterpret_cast<const C*>(a.tw_y);
-    fft_fwd<C, 1, false, SB>(d, lx, ly, 1, nx, 0, twx);   // rows (x index fastest across threads)
-    fft_fwd<C, 1, true, SB>(d, ly, lx, nx, 1, 0, twy);    // columns (column index fastest)
+    const R one = twx[0].x;
+    fft_fwd<C, 1, false, SBX>(d, lx, ly, 1, nx, 0, twx);   // rows (x index fastest across threads)
+    fft_fwd<C, 1, true, SBY>(d, ly, lx, nx, 1, 0, twy);    // columns (column index fastest)
     const C mu = reinterpret_cast<const C*>(a.mu_dT)[blockIdx.x];
     const C* sx = reinterpret_cast<const C*>(a.sig_x);
     const C* sy = reinterpret_cast<const C*>(a.sig_y);
     for (long i = threadIdx.x; i < N; i += blockDim.x) {
         const int ky = (int)(i >> lx), kx = (int)(i & (nx - 1));
-        const long slot = ((long)digitrev<SB>(ky, ly) << lx) + digitrev<SB>(kx, lx);
-        d[slot] = shift_div(d[slot], mu, cadd(sx[kx], sy[ky]));
+        const long slot = ((long)digitrev<SBY>(ky, ly) << lx) + digitrev<SBX>(kx, lx);
+        d[slot] = div_one_minus(d[slot], cmul(mu, cadd(sx[kx], sy[ky])), one);
     }
     __syncthreads();
-    fft_inv<C, 1, true, SB>(d, ly, lx, nx, 1, 0, twy);
-    fft_inv<C, 1, false, SB>(d, lx, ly, 1, nx, 0, twx);
+    fft_inv<C, 1, true, SBY>(d, ly, lx, nx, 1, 0, twy);
+    fft_inv<C, 1, false, SBX>(d, lx, ly, 1, nx, 0, twx);
     const R sc = (R)1 / (R)N;
     for (long i = threadIdx.x; i < N; i += blockDim.x) x[i] = cscale(d[i], sc);
 }
 
 // Row pass of the three-pass 2D path: rows_per_block contiguous rows of length
 // nx; forward FFT, or inverse FFT with the 1/(nx ny) normalisation.
-template <typename R>
+template <typename R, int SBX>
 __global__ void __launch_bounds__(256) k_space_rows(SpaceArgs a, int inverse) {
     typedef typename Cx<R>::T C;
-    constexpr int SB = sizeof(R) == 8 ? 4 : 3;   // radix 16 in FP64, radix 8 in FP32 (register pressure)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* d = reinterpret_cast<C*>(smem_raw);
     const int nx = a.nx, rpb = a.rows_per_block;
@@ -100,13 +120,13 @@ __global__ void __launch_bounds__(256) k_space_rows(SpaceArgs a, int inverse) {
     __syncthreads();
     const C* tw = reinterpret_cast<const C*>(a.tw_x);
     if (!inverse) {
-        fft_fwd<C, 1, true, SB>(d, a.lognx, logr, ld, 1, 0, tw);
+        fft_fwd<C, 1, true, SBX>(d, a.lognx, logr, ld, 1, 0, tw);
         for (long i = threadIdx.x; i < cnt; i += blockDim.x) {
             const int row = (int)(i >> a.lognx), ix = (int)(i & (nx - 1));
             x[i] = d[ix * ld + row];
         }
     } else {
-        fft_inv<C, 1, true, SB>(d, a.lognx, logr, ld, 1, 0, tw);
+        fft_inv<C, 1, true, SBX>(d, a.lognx, logr, ld, 1, 0, tw);
         const R sc = (R)1 / ((R)nx * (R)a.ny);
         for (long i = threadIdx.x; i < cnt; i += blockDim.x) {
             const int row = (int)(i >> a.lognx), ix = (int)(i & (nx - 1));
@@ -115,12 +135,14 @@ __global__ void __launch_bounds__(256) k_space_rows(SpaceArgs a, int inverse) {
     }
 }
 
-// Column pass: a tile of W consecutive x slots (digit-reversed order) times
-// all ny rows of one plane; forward FFT along y, divide, inverse FFT along y.
-template <typename R>
+// Column pass: a tile of W consecutive x slots (digit-reversed order of the
+// row pass's plan SBX) times all ny rows of one plane; forward FFT along y,
+// divide, inverse FFT along y.  The products mu sigma_x and mu sigma_y of
+// the tile's x slots and of every y slot are formed once per CTA, so the
+// division needs only their sum per point.
+template <typename R, int SBX, int SBY>
 __global__ void __launch_bounds__(256) k_space_cols(SpaceArgs a) {
     typedef typename Cx<R>::T C;
-    constexpr int SB = sizeof(R) == 8 ? 4 : 3;   // radix 16 in FP64, radix 8 in FP32 (register pressure)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* d = reinterpret_cast<C*>(smem_raw);
     const int nx = a.nx, ny = a.ny, W = a.cols_per_block;
@@ -134,28 +156,35 @@ __global__ void __launch_bounds__(256) k_space_cols(SpaceArgs a) {
         const int iy = (int)(i >> logW), w = (int)(i & (W - 1));
         d[i] = x[(long)iy * nx + w];
     }
-    __syncthreads();
-    const C* twy = reinterpret_cast<const C*>(a.tw_y);
-    fft_fwd<C, 1, true, SB>(d, a.logny, logW, W, 1, 0, twy);
     const C mu = reinterpret_cast<const C*>(a.mu_dT)[plane];
     const C* sx = reinterpret_cast<const C*>(a.sig_x);
     const C* sy = reinterpret_cast<const C*>(a.sig_y);
-    // symbol of the x slots of this tile and of every y slot
-    C* sxs = d + cnt;                 // W entries
-    C* sys = sxs + W;                 // ny entries, indexed by y slot
-    for (int i = threadIdx.x; i < W; i += blockDim.x) sxs[i] = sx[slot_freq<SB>(c0 + i, a.lognx)];
-    for (int i = threadIdx.x; i < ny; i += blockDim.x) sys[i] = sy[slot_freq<SB>(i, a.logny)];
+    C* mx = d + cnt;                  // W entries: mu sigma_x of this tile's x slots
+    C* my = mx + W;                   // ny entries: mu sigma_y per y slot
+    for (int i = threadIdx.x; i < W; i += blockDim.x) mx[i] = cmul(mu, sx[slot_freq<SBX>(c0 + i, a.lognx)]);
+    for (int i = threadIdx.x; i < ny; i += blockDim.x) my[i] = cmul(mu, sy[slot_freq<SBY>(i, a.logny)]);
     __syncthreads();
+    const C* twy = reinterpret_cast<const C*>(a.tw_y);
+    const R one = twy[0].x;
+    fft_fwd<C, 1, true, SBY>(d, a.logny, logW, W, 1, 0, twy);
     for (long i = threadIdx.x; i < cnt; i += blockDim.x) {
         const int ys = (int)(i >> logW), w = (int)(i & (W - 1));
-        d[i] = shift_div(d[i], mu, cadd(sxs[w], sys[ys]));
+        d[i] = div_one_minus(d[i], cadd(mx[w], my[ys]), one);
     }
     __syncthreads();
-    fft_inv<C, 1, true, SB>(d, a.logny, logW, W, 1, 0, twy);
+    fft_inv<C, 1, true, SBY>(d, a.logny, logW, W, 1, 0, twy);
     for (long i = threadIdx.x; i < cnt; i += blockDim.x) {
         const int iy = (int)(i >> logW), w = (int)(i & (W - 1));
         x[(long)iy * nx + w] = d[i];
     }
+}
+
+// The radix plan of a length-2^logn transform in the precision R (see the
+// file comment).
+template <typename R>
+static int plan_bits(int logn) {
+    if (sizeof(R) == 4) return 3;
+    return (logn == 6 || logn == 9) ? 3 : 4;
 }
 
 template <typename K>
@@ -163,47 +192,81 @@ static cudaError_t set_smem(K kern, size_t smem) {
     return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-template <typename R>
-cudaError_t launch_space_1d(const SpaceArgs& a, cudaStream_t st) {
+template <typename R, int SB>
+static cudaError_t launch_1d_sb(const SpaceArgs& a, cudaStream_t st) {
     typedef typename Cx<R>::T C;
     size_t smem = sizeof(C) * (size_t)a.nx;
-    cudaError_t e = set_smem(k_space_1d<R>, smem);
+    cudaError_t e = set_smem(k_space_1d<R, SB>, smem);
     if (e != cudaSuccess) return e;
-    k_space_1d<R><<<a.planes, 512, smem, st>>>(a);
+    k_space_1d<R, SB><<<a.planes, 512, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_space_1d(const SpaceArgs& a, cudaStream_t st) {
+    if constexpr (sizeof(R) == 4) return launch_1d_sb<R, 3>(a, st);
+    else return plan_bits<R>(a.lognx) == 3 ? launch_1d_sb<R, 3>(a, st) : launch_1d_sb<R, 4>(a, st);
+}
+
+template <typename R, int SBX, int SBY>
+static cudaError_t launch_2d_small_sb(const SpaceArgs& a, cudaStream_t st) {
+    typedef typename Cx<R>::T C;
+    size_t smem = sizeof(C) * (size_t)a.nx * a.ny;
+    cudaError_t e = set_smem(k_space_2d_small<R, SBX, SBY>, smem);
+    if (e != cudaSuccess) return e;
+    k_space_2d_small<R, SBX, SBY><<<a.planes, 512, smem, st>>>(a);
     return cudaGetLastError();
 }
 
 template <typename R>
 cudaError_t launch_space_2d_small(const SpaceArgs& a, cudaStream_t st) {
+    if constexpr (sizeof(R) == 4) {
+        return launch_2d_small_sb<R, 3, 3>(a, st);
+    } else {
+        const int bx = plan_bits<R>(a.lognx), by = plan_bits<R>(a.logny);
+        if (bx == 3) return by == 3 ? launch_2d_small_sb<R, 3, 3>(a, st) : launch_2d_small_sb<R, 3, 4>(a, st);
+        return by == 3 ? launch_2d_small_sb<R, 4, 3>(a, st) : launch_2d_small_sb<R, 4, 4>(a, st);
+    }
+}
+
+template <typename R, int SBX>
+static cudaError_t launch_rows_sb(const SpaceArgs& a, int inverse, cudaStream_t st) {
     typedef typename Cx<R>::T C;
-    size_t smem = sizeof(C) * (size_t)a.nx * a.ny;
-    cudaError_t e = set_smem(k_space_2d_small<R>, smem);
+    size_t smem = sizeof(C) * (size_t)a.nx * (a.rows_per_block + 1);
+    cudaError_t e = set_smem(k_space_rows<R, SBX>, smem);
     if (e != cudaSuccess) return e;
-    k_space_2d_small<R><<<a.planes, 512, smem, st>>>(a);
+    long rows = (long)a.planes * a.ny;
+    int grid = (int)(rows / a.rows_per_block);
+    k_space_rows<R, SBX><<<grid, 256, smem, st>>>(a, inverse);
     return cudaGetLastError();
 }
 
 template <typename R>
 cudaError_t launch_space_rows(const SpaceArgs& a, int inverse, cudaStream_t st) {
+    if constexpr (sizeof(R) == 4) return launch_rows_sb<R, 3>(a, inverse, st);
+    else return plan_bits<R>(a.lognx) == 3 ? launch_rows_sb<R, 3>(a, inverse, st) : launch_rows_sb<R, 4>(a, inverse, st);
+}
+
+template <typename R, int SBX, int SBY>
+static cudaError_t launch_cols_sb(const SpaceArgs& a, cudaStream_t st) {
     typedef typename Cx<R>::T C;
-    size_t smem = sizeof(C) * (size_t)a.nx * (a.rows_per_block + 1);
-    cudaError_t e = set_smem(k_space_rows<R>, smem);
+    size_t smem = sizeof(C) * ((size_t)a.ny * a.cols_per_block + a.cols_per_block + a.ny);
+    cudaError_t e = set_smem(k_space_cols<R, SBX, SBY>, smem);
     if (e != cudaSuccess) return e;
-    long rows = (long)a.planes * a.ny;
-    int grid = (int)(rows / a.rows_per_block);
-    k_space_rows<R><<<grid, 256, smem, st>>>(a, inverse);
+    int grid = a.planes * (a.nx / a.cols_per_block);
+    k_space_cols<R, SBX, SBY><<<grid, 256, smem, st>>>(a);
     return cudaGetLastError();
 }
 
 template <typename R>
 cudaError_t launch_space_cols(const SpaceArgs& a, cudaStream_t st) {
-    typedef typename Cx<R>::T C;
-    size_t smem = sizeof(C) * ((size_t)a.ny * a.cols_per_block + a.cols_per_block + a.ny);
-    cudaError_t e = set_smem(k_space_cols<R>, smem);
-    if (e != cudaSuccess) return e;
-    int grid = a.planes * (a.nx / a.cols_per_block);
-    k_space_cols<R><<<grid, 256, smem, st>>>(a);
-    return cudaGetLastError();
+    if constexpr (sizeof(R) == 4) {
+        return launch_cols_sb<R, 3, 3>(a, st);
+    } else {
+        const int bx = plan_bits<R>(a.lognx), by = plan_bits<R>(a.logny);
+        if (bx == 3) return by == 3 ? launch_cols_sb<R, 3, 3>(a, st) : launch_cols_sb<R, 3, 4>(a, st);
+        return by == 3 ? launch_cols_sb<R, 4, 3>(a, st) : launch_cols_sb<R, 4, 4>(a, st);
+    }
 }
 
 template cudaError_t launch_space_1d<float>(const SpaceArgs&, cudaStream_t);

@@ -116,6 +116,30 @@ def test_fig1_advection_setup_1d(inner):
 
 
 @pytest.mark.parametrize("inner", ["gmres", "bicgstab"])
+def test_fig1_advection_setup_2d(inner):
+    """Fig. 1's setup in 2D, as the paper runs it: eq. (advection)
+    u_t + u_x + u_y = 0 on the periodic unit square with N = 700^2 points,
+    5th-order upwind stencils, L = 64, M = 3, T = 0.0128, Krylov inner solves
+    at tau = 1e-15 (GMRES, the paper's, and BiCGStab; 700 is not a power of
+    two).  All 192 blocks of the space-time solution against the Fourier
+    closed form, the last step against the exact solution at 1e-12."""
+    torch = torch_cuda()
+    from paper_2103_12571_gb300.api import Plan
+    L, M = 64, 3
+    prob, u0, exact = _advection(2, 700, 5, M, L, 0.0128)
+    Q, A, dT = oracle_setup(prob)
+    plan = Plan(prob, precision="c128", inner=inner, tau=1e-15, alpha="paper", max_iter=30)
+    u, st = plan.solve(to_dev(torch, u0), tol=1e-14, raise_on_fail=False)
+    num = den = 0.0
+    for l, m, ref in fourier.modal_blocks(u0, prob, Q, dT, L):
+        d = u[l, m].cpu().numpy() - ref
+        num += float(d @ d)
+        den += float(ref @ ref)
+    assert (num / den) ** 0.5 < 1e-11, ((num / den) ** 0.5, st)
+    assert np.max(np.abs(u[-1, -1].cpu().numpy() - exact)) < 1e-12, st
+
+
+@pytest.mark.parametrize("inner", ["gmres", "bicgstab"])
 @pytest.mark.parametrize("tol,N,order,M,L,tau", [(1e-5, 350, 2, 2, 8, 1e-8), (1e-9, 350, 4, 2, 16, 1e-11),
                                                  (1e-12, 600, 5, 3, 32, 1e-14)])
 def test_paper_advection_table1(tol, N, order, M, L, tau, inner):
