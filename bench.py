@@ -187,11 +187,11 @@ def source_hash():
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
 
 
-def measured_traffic(kind, precision, points, path=None):
+def measured_traffic(kind, precision, alg_bytes, path=None):
     """DRAM bytes per launch of a kernel kind from the last ncu capture (taken
-    on a smaller case of the same kernel and scaled by the transform points a
-    launch processes), if the capture was taken on the current kernel
-    sources; else None."""
+    on a smaller case of the same kernel and scaled by the ratio of
+    algorithmic bytes, i.e. by the units a launch processes), if the capture
+    was taken on the current kernel sources; else None."""
     try:
         t = json.load(open(path or TRAFFIC_FILE))
     except (OSError, ValueError):
@@ -201,7 +201,7 @@ def measured_traffic(kind, precision, points, path=None):
     e = t.get("kernels", {}).get("%s@%s" % (kind, precision))
     if not e:
         return None
-    return e["dram_bytes"] * points / e["points"]
+    return e["dram_bytes"] * alg_bytes / e["alg_bytes"]
 
 
 def peaks():
@@ -274,7 +274,9 @@ def roofline(kind, prof_row, counts, precision, fp64_measured_tflops):
                 "algorithmic_bytes_per_launch": c["bytes"]}
     roof["kernel"] = kind
     roof["kernel_ms"] = per
-    roof["traffic"] = measured_traffic(kind, precision, c["points"])
+    roof["traffic"] = measured_traffic(kind, precision, c["bytes"])
+    roof["traffic_source"] = "profiles/traffic.json (ncu dram__bytes_read.sum + dram__bytes_write.sum on the same grid " \
+                             "with L = 64, scaled by algorithmic bytes)"
     return roof
 
 

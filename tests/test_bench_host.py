@@ -70,12 +70,12 @@ def test_dominant_kernel_splits_the_three_pass_solve():
 def test_traffic_is_scaled_and_null_when_the_kernel_sources_changed(tmp_path, monkeypatch):
     path = tmp_path / "traffic.json"
     path.write_text(json.dumps({"source_sha256": "a" * 64,
-                                "kernels": {"space_cols@c128": {"dram_bytes": 1000.0, "points": 10}}}))
+                                "kernels": {"space_cols@c128": {"dram_bytes": 1000.0, "alg_bytes": 1100.0}}}))
     monkeypatch.setattr(bench, "source_hash", lambda: "a" * 64)
-    assert bench.measured_traffic("space_cols", "c128", 40, str(path)) == pytest.approx(4000.0)
-    assert bench.measured_traffic("space_rows", "c128", 40, str(path)) is None
+    assert bench.measured_traffic("space_cols", "c128", 4400.0, str(path)) == pytest.approx(4000.0)
+    assert bench.measured_traffic("space_rows", "c128", 4400.0, str(path)) is None
     monkeypatch.setattr(bench, "source_hash", lambda: "0" * 64)
-    assert bench.measured_traffic("space_cols", "c128", 40, str(path)) is None
+    assert bench.measured_traffic("space_cols", "c128", 4400.0, str(path)) is None
 
 
 def test_reference_arm_prints_the_contract_line():
