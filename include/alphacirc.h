@@ -62,6 +62,11 @@ extern "C" {
                                  whose right-hand side differs from w only by -alpha H u_L^k in block 1;
                                  requires AC_STOP_PAPER                                                   */
 
+#define AC_UPDATE_PLAIN 0  /* update kernel: tiles read straight from global memory (default)      */
+#define AC_UPDATE_TMA   1  /* complex64 plans: persistent update kernel whose X and u tiles the copy
+                              engine stages in shared memory as 2D tensor tiles (double-buffered);
+                              used when u is 16-byte aligned and two CTAs' buffers fit an SM     */
+
 #define AC_MAX_STATS 128
 
 /* Spatial operator A = nu * Lap_h - cx * D_x - cy * D_y on the periodic box
@@ -101,6 +106,7 @@ typedef struct {
                            Arnoldi steps over all restarts                              */
     int form;           /* AC_FORM_CORRECTION | AC_FORM_PAPER                           */
     int inner_restart;  /* GMRES restart length m, 1..32 (<= 0: 30)                     */
+    int update_kernel;  /* AC_UPDATE_PLAIN | AC_UPDATE_TMA                              */
 } ac_alpha_schedule;
 
 /* Per-solve record (host memory, filled by the solve calls). */
@@ -126,6 +132,9 @@ typedef struct {
                                          3: BiCGStab, 4: GMRES                                               */
     long long workspace_bytes;        /* device memory owned by the plan               */
     long long launches;               /* kernels launched by this plan so far          */
+    int update_kernel;                /* AC_UPDATE_TMA if the TMA-staged update kernel is in use
+                                         (requested and applicable), else AC_UPDATE_PLAIN   */
+    int update_tile_tma;              /* grid points per tile of the TMA-staged kernel (0 if unused) */
 } ac_plan_info;
 
 typedef struct ac_plan ac_plan;

@@ -22,6 +22,7 @@ from math import factorial
 
 from .collocation import H_matrix
 from .operators import apply_C, rhs_w
+from .sequential import ordering
 
 
 def lemma1(L, alpha):
@@ -74,7 +75,8 @@ def precond_solve(A, Q, dT, alpha, r):
     d = eigenvalues_d(L, alpha)
     y = np.empty_like(x)
     for l in range(L):
-        lu = spla.splu(block_matrix(A, Q, dT, d[l]).astype(np.complex128))
+        # the block has the sparsity pattern of C_coll: the same ordering
+        lu = spla.splu(block_matrix(A, Q, dT, d[l]).astype(np.complex128), permc_spec=ordering(A))
         y[l] = lu.solve(x[l].reshape(-1)).reshape(M, N)
     return time_inverse(y, alpha)
 

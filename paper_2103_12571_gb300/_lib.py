@@ -23,6 +23,7 @@ AC_INNER_FFT, AC_INNER_BICGSTAB, AC_INNER_GMRES = 0, 1, 2
 AC_ALPHA_FIXED, AC_ALPHA_PAPER, AC_ALPHA_MIXED = 0, 1, 2
 AC_STOP_RESIDUAL, AC_STOP_PAPER = 0, 1
 AC_FORM_CORRECTION, AC_FORM_PAPER = 0, 1
+AC_UPDATE_PLAIN, AC_UPDATE_TMA = 0, 1
 AC_MAX_STATS = 128
 
 
@@ -36,7 +37,8 @@ class Problem(ctypes.Structure):
 class Schedule(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int), ("alpha0", ctypes.c_double), ("m0", ctypes.c_double),
                 ("tau", ctypes.c_double), ("max_iter", ctypes.c_int), ("stop_rule", ctypes.c_int),
-                ("inner_max_iter", ctypes.c_int), ("form", ctypes.c_int), ("inner_restart", ctypes.c_int)]
+                ("inner_max_iter", ctypes.c_int), ("form", ctypes.c_int), ("inner_restart", ctypes.c_int),
+                ("update_kernel", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -51,7 +53,8 @@ class Stats(ctypes.Structure):
 class PlanInfo(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int), ("M", ctypes.c_int), ("L", ctypes.c_int), ("F", ctypes.c_int),
                 ("tile_fwd", ctypes.c_int), ("tile_upd", ctypes.c_int), ("spatial_path", ctypes.c_int),
-                ("workspace_bytes", ctypes.c_longlong), ("launches", ctypes.c_longlong)]
+                ("workspace_bytes", ctypes.c_longlong), ("launches", ctypes.c_longlong),
+                ("update_kernel", ctypes.c_int), ("update_tile_tma", ctypes.c_int)]
 
 
 _P = ctypes.c_void_p

@@ -39,6 +39,7 @@ INNER = {"fft": C.AC_INNER_FFT, "bicgstab": C.AC_INNER_BICGSTAB, "gmres": C.AC_I
 ALPHA = {"fixed": C.AC_ALPHA_FIXED, "paper": C.AC_ALPHA_PAPER, "mixed": C.AC_ALPHA_MIXED}
 STOP = {"residual": C.AC_STOP_RESIDUAL, "paper": C.AC_STOP_PAPER}
 FORM = {"correction": C.AC_FORM_CORRECTION, "paper": C.AC_FORM_PAPER}
+UPDATE = {"plain": C.AC_UPDATE_PLAIN, "tma": C.AC_UPDATE_TMA}
 
 
 def stats_dict(st):
@@ -54,7 +55,7 @@ class Plan:
 
     def __init__(self, prob, M=None, L=None, dT=None, precision="c128", inner="fft", alpha="paper",
                  alpha0=1e-4, m0=0.0, tau=0.0, max_iter=50, stop="residual", inner_max_iter=0,
-                 form="correction", inner_restart=0):
+                 form="correction", inner_restart=0, update_kernel="plain"):
         M = int(M if M is not None else prob["M"])
         L = int(L if L is not None else prob["L"])
         dT = float(dT if dT is not None else prob["T"] / L)
@@ -63,7 +64,8 @@ class Plan:
         self.prob = dict(prob)
         sched = C.Schedule(mode=ALPHA[alpha], alpha0=float(alpha0), m0=float(m0), tau=float(tau),
                            max_iter=int(max_iter), stop_rule=STOP[stop], inner_max_iter=int(inner_max_iter),
-                           form=FORM[form], inner_restart=int(inner_restart))
+                           form=FORM[form], inner_restart=int(inner_restart),
+                           update_kernel=UPDATE[update_kernel])
         handle = ctypes.c_void_p()
         C.check(C.lib().ac_setup(ctypes.byref(make_problem(prob)), M, L, dT, ctypes.byref(sched),
                                  PRECISION[precision], INNER[inner], ctypes.byref(handle)), "ac_setup")

@@ -2,6 +2,8 @@
 // management and the launch sequences of Algorithm 1 (one iteration), the
 // Richardson loop with the alpha rules of Sec. 3.3 / Algorithm 2, the adjoint
 // solve and the gradient contractions.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -9,6 +11,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -101,6 +104,15 @@ struct ac_plan {
     void* d_bicg = nullptr;      // Krylov vectors when they do not fit in shared memory
     double2* d_mu64 = nullptr;   // complex64 BiCGStab: dT mu in FP64 (reliable updates)
     double2* d_x64 = nullptr;    // complex64 BiCGStab: FP64 solution accumulators, F*M*N
+    // TMA-staged update kernel (complex64 plans, correction form)
+    bool tma_ok = false;
+    int tma_P = 0, tma_grid = 0;
+    ac::UpdTmaGeom tgeo{};
+    CUtensorMap mapX{};                  // X as [F*M rows][2N floats]
+    CUtensorMap mapU{};                  // the last u as [L*M rows][N doubles]
+    const void* mapU_ptr = nullptr;
+    int* d_err = nullptr;                // set by a kernel whose bounded wait timed out
+    int upd_grid_used = 0;               // partial results written by the last update launch
     int* d_iters = nullptr;      // Krylov iterations per system
     int* h_iters = nullptr;      // pinned copy
     double* h_part_fwd = nullptr;  // pinned
@@ -330,6 +342,89 @@ static int run_spatial(ac_plan* p, void* X, const void* mu_dT, int planes, int t
     return AC_OK;
 }
 
+// ----------------------------------------------------- TMA tensor maps
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library).
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    });
+    return fn;
+}
+
+// 2D tensor map over rows x inner elements (row stride inner * esize bytes)
+// with boxes of box_rows x box_inner elements, no swizzle, zero fill.
+static bool encode_2d(CUtensorMap* m, CUtensorMapDataType dt, size_t esize, const void* base, uint64_t inner,
+                      uint64_t rows, uint32_t box_inner, uint32_t box_rows) {
+    PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t dims[2] = {inner, rows};
+    const cuuint64_t strides[1] = {inner * esize};
+    const cuuint32_t box[2] = {box_inner, box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    return fn(m, dt, 2, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+static size_t round128(size_t v) { return (v + 127) & ~size_t(127); }
+
+// Tile geometry of the TMA-staged update kernel for tiles of P points: the
+// X rows (F*M) and u rows (L*M) of a tile in boxes of at most 256 rows, two
+// buffers of each and the transform buffer within 113 KB (two CTAs per SM).
+static bool tma_geometry(const ac_plan* p, int P, ac::UpdTmaGeom* g) {
+    const int FM = p->F * p->M, LM = p->L * p->M;
+    if (P < 8 || P > 128 || p->N % P != 0 || (p->N & 1)) return false;
+    g->ntiles = p->N / P;
+    g->xboxes = (FM + 255) / 256;
+    g->xrows = (FM + g->xboxes - 1) / g->xboxes;
+    g->uboxes = (LM + 255) / 256;
+    g->urows = (LM + g->uboxes - 1) / g->uboxes;
+    const size_t xb = (size_t)g->xboxes * g->xrows * P * sizeof(float2);
+    const size_t ub = (size_t)g->uboxes * g->urows * P * sizeof(double);
+    g->tile_bytes = (unsigned)(xb + ub);
+    g->xbuf = (unsigned)round128(xb);
+    g->ubuf = (unsigned)round128(ub);
+    g->zbuf = (unsigned)round128((size_t)LM * (P / 2) * sizeof(float2));
+    return 2 * ((size_t)g->xbuf + g->ubuf) + g->zbuf <= 113 * 1024;
+}
+
+// On request (AC_UPDATE_TMA), chooses the TMA tile (the largest that fits)
+// and encodes the map of X; leaves tma_ok false when the kernel does not
+// apply.  Not the default: on the 2D heat workloads it measured slower than
+// the plain update kernel (256^2, L = 64: 87-118 us against 74-76 us; 128^2,
+// L = 32: 18-27 us against 16.3 us), whose four CTAs per SM hide the global
+// latency as well as the staged double buffers of two.
+static void setup_tma(ac_plan* p) {
+    p->tma_ok = false;
+    if (p->precision != AC_C64 || p->sched.update_kernel != AC_UPDATE_TMA) return;
+    for (int P = 64; P >= 8; P >>= 1) {
+        ac::UpdTmaGeom g{};
+        if (!tma_geometry(p, P, &g)) continue;
+        g.err = p->d_err;
+        const int per_sm = ac::upd_tma_ctas_per_sm(p->M, g);
+        int dev = 0, sms = 0;
+        if (per_sm < 1 || cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return;
+        if (!encode_2d(&p->mapX, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, sizeof(float), p->X, 2 * (uint64_t)p->N,
+                       (uint64_t)p->F * p->M, (uint32_t)(2 * P), (uint32_t)g.xrows))
+            return;
+        p->tgeo = g;
+        p->tma_P = P;
+        p->tma_grid = std::min(g.ntiles, per_sm * sms);
+        p->tma_ok = true;
+        return;
+    }
+}
+
 // ------------------------------------------------------ one preconditioner
 // out (+)= C_alpha^{-1} (w - C u)   [u may be null: out (+)= C_alpha^{-1} w]
 template <typename R>
@@ -393,9 +488,25 @@ static int stage_b(ac_plan* p, double* out, int accumulate, cudaStream_t st, int
     ua.accumulate = accumulate;
     ua.diff_last = diff_last;
     ua.part = p->d_part_upd;
+    // the TMA-staged kernel for u += e on an aligned u (the map of u is
+    // encoded once per u buffer)
+    const bool tma = p->tma_ok && sizeof(R) == 4 && accumulate && !diff_last && ((uintptr_t)out & 15) == 0;
+    if (tma && p->mapU_ptr != out) {
+        if (!encode_2d(&p->mapU, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, sizeof(double), out, (uint64_t)p->N,
+                       (uint64_t)p->L * p->M, (uint32_t)p->tma_P, (uint32_t)p->tgeo.urows))
+            return fail(AC_ERR_CUDA, "cuTensorMapEncodeTiled failed for u");
+        p->mapU_ptr = out;
+    }
     {
         ProfScope ps(p, KK_UPD, st);
-        CK(ac::launch_upd<R>(ua, p->grid_upd, smem, st));
+        if (tma) {
+            ua.P = p->tma_P;
+            CK(ac::launch_upd_tma(&p->mapX, &p->mapU, ua, p->tgeo, p->tma_grid, st));
+            p->upd_grid_used = p->tma_grid;
+        } else {
+            CK(ac::launch_upd<R>(ua, p->grid_upd, smem, st));
+            p->upd_grid_used = p->grid_upd;
+        }
         p->launches++;
     }
     return AC_OK;
@@ -511,6 +622,17 @@ static int inner_summary(const ac_plan* p, int* failed) {
     return worst;
 }
 
+// Reads (and clears) the kernels' error flag; the stream must be synchronised.
+static int kernel_flag(ac_plan* p) {
+    int h = 0;
+    CK(cudaMemcpy(&h, p->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h) {
+        CK(cudaMemset(p->d_err, 0, sizeof(int)));
+        return fail(AC_ERR_CUDA, "a wait on the copy engine in the update kernel timed out");
+    }
+    return AC_OK;
+}
+
 // The Richardson loop shared by the forward and the adjoint solve.
 static int richardson_loop(ac_plan* p, const double* u0, const double* b, int b_rev, int transposed, double* u,
                            double tol, ac_stats* stats, cudaStream_t st) {
@@ -572,11 +694,11 @@ static int richardson_loop(ac_plan* p, const double* u0, const double* b, int b_
             if (rc) return rc;
             rc = precond_b(p, u, 0, st, 1);
             if (rc) return rc;
-            CK(cudaMemcpyAsync(p->h_part_upd, p->d_part_upd, sizeof(double) * p->grid_upd, cudaMemcpyDeviceToHost, st));
+            CK(cudaMemcpyAsync(p->h_part_upd, p->d_part_upd, sizeof(double) * p->upd_grid_used, cudaMemcpyDeviceToHost, st));
             CK(cudaStreamSynchronize(st));
             double mx = 0.0;
-            for (int i = 0; i < p->grid_upd; ++i) mx = std::max(mx, p->h_part_upd[i]);
-            for (int i = 0; i < p->grid_upd; ++i)
+            for (int i = 0; i < p->upd_grid_used; ++i) mx = std::max(mx, p->h_part_upd[i]);
+            for (int i = 0; i < p->upd_grid_used; ++i)
                 if (std::isnan(p->h_part_upd[i])) mx = p->h_part_upd[i];
             S->alpha[k] = alpha;
             S->m[k] = sc.mode == AC_ALPHA_PAPER ? m : 0.0;
@@ -681,16 +803,18 @@ static int richardson_loop(ac_plan* p, const double* u0, const double* b, int b_
         if (rc) return rc;
         if (sc.mode == AC_ALPHA_PAPER) m = m_next;
         if (sc.stop_rule == AC_STOP_PAPER) {
-            CK(cudaMemcpyAsync(p->h_part_upd, p->d_part_upd, sizeof(double) * p->grid_upd, cudaMemcpyDeviceToHost, st));
+            CK(cudaMemcpyAsync(p->h_part_upd, p->d_part_upd, sizeof(double) * p->upd_grid_used, cudaMemcpyDeviceToHost, st));
             CK(cudaStreamSynchronize(st));
             double mx = 0.0;
-            for (int i = 0; i < p->grid_upd; ++i) mx = std::max(mx, p->h_part_upd[i]);
-            for (int i = 0; i < p->grid_upd; ++i)
+            for (int i = 0; i < p->upd_grid_used; ++i) mx = std::max(mx, p->h_part_upd[i]);
+            for (int i = 0; i < p->upd_grid_used; ++i)
                 if (std::isnan(p->h_part_upd[i])) mx = p->h_part_upd[i];
             S->diff_last[k] = mx;
         }
     }
     CK(cudaStreamSynchronize(st));
+    rc = kernel_flag(p);
+    if (rc) return rc;
     return S->converged ? AC_OK : fail(AC_ERR_NO_CONVERGENCE, "stop rule not met after %d iterations", S->iters);
 }
 
@@ -820,7 +944,7 @@ void ac_destroy(ac_plan* p) {
     void* bufs[] = {p->X, p->tw_L, p->tw_x, p->tw_y, p->sig_x, p->sig_y, p->sigT_x, p->sigT_y,
                     p->d_qs, p->d_s, p->d_wnorm, p->d_sinv, p->d_Sinv, p->d_P, p->d_mu,
                     p->d_part_fwd, p->d_part_upd, p->d_part_d, p->d_dtQ, p->d_dtQT, p->d_bicg,
-                    p->d_iters, p->d_mu64, p->d_x64};
+                    p->d_iters, p->d_mu64, p->d_x64, p->d_err};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (p->h_part_fwd) cudaFreeHost(p->h_part_fwd);
@@ -941,11 +1065,12 @@ int ac_setup(const ac_problem* prob, int M, int L, double dT, const ac_alpha_sch
     AL(p->d_P, (size_t)F * M * M * cs);
     AL(p->d_mu, (size_t)F * M * cs);
     AL(p->d_part_fwd, sizeof(double) * p->grid);
-    AL(p->d_part_upd, sizeof(double) * p->grid_upd);
+    AL(p->d_part_upd, sizeof(double) * std::max(p->grid_upd, 8 * 152));
     p->part_d_len = std::max(2 * 152 * 2, 3 * 152 * 4);
     AL(p->d_part_d, sizeof(double) * p->part_d_len);
     AL(p->d_dtQ, sizeof(double) * M * M);
     AL(p->d_dtQT, sizeof(double) * M * M);
+    AL(p->d_err, sizeof(int));
     if (p->spatial_path == 3) {
         AL(p->d_iters, sizeof(int) * F * M);
         if (6 * cs * (size_t)p->N > 200 * 1024) AL(p->d_bicg, 6 * cs * (size_t)p->N * F * M);
@@ -960,7 +1085,7 @@ int ac_setup(const ac_problem* prob, int M, int L, double dT, const ac_alpha_sch
     }
 #undef AL
     if (e == cudaSuccess) e = cudaMallocHost((void**)&p->h_part_fwd, sizeof(double) * p->grid);
-    if (e == cudaSuccess) e = cudaMallocHost((void**)&p->h_part_upd, sizeof(double) * p->grid_upd);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&p->h_part_upd, sizeof(double) * std::max(p->grid_upd, 8 * 152));
     if (e == cudaSuccess) e = cudaMallocHost((void**)&p->h_part_d, sizeof(double) * p->part_d_len);
     if (e == cudaSuccess && p->spatial_path >= 3) e = cudaMallocHost((void**)&p->h_iters, sizeof(int) * F * M);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_res, cudaEventDisableTiming);  // spin: low latency
@@ -1004,11 +1129,14 @@ int ac_setup(const ac_problem* prob, int M, int L, double dT, const ac_alpha_sch
     if (rc == AC_OK && (cudaMemcpy(p->d_dtQ, dtQ, sizeof(double) * M * M, cudaMemcpyHostToDevice) != cudaSuccess ||
                         cudaMemcpy(p->d_dtQT, dtQT, sizeof(double) * M * M, cudaMemcpyHostToDevice) != cudaSuccess))
         rc = fail(AC_ERR_CUDA, "table upload failed");
+    if (rc == AC_OK && cudaMemset(p->d_err, 0, sizeof(int)) != cudaSuccess) rc = fail(AC_ERR_CUDA, "set-up failed");
     if (rc == AC_OK && cudaDeviceSynchronize() != cudaSuccess) rc = fail(AC_ERR_CUDA, "set-up sync failed");
     if (rc != AC_OK) {
         ac_destroy(p);
         return rc;
     }
+    p->upd_grid_used = p->grid_upd;
+    setup_tma(p);
     *out = p;
     return AC_OK;
 }
@@ -1024,6 +1152,8 @@ int ac_plan_get_info(const ac_plan* p, ac_plan_info* info) {
     info->spatial_path = p->spatial_path;
     info->workspace_bytes = p->workspace;
     info->launches = p->launches;
+    info->update_kernel = p->tma_ok ? AC_UPDATE_TMA : AC_UPDATE_PLAIN;
+    info->update_tile_tma = p->tma_ok ? p->tma_P : 0;
     return AC_OK;
 }
 

@@ -21,6 +21,7 @@
 #include "fft.cuh"
 #include "kernels.h"
 #include "norm2.cuh"
+#include "tma.cuh"
 
 namespace ac {
 
@@ -351,6 +352,126 @@ __global__ void __launch_bounds__(256) k_upd(UpdArgs a) {
         const double v = __longlong_as_double((long long)mx);
         a.part[blockIdx.x] = a.diff_last ? v : v * a.sinv[L - 1];
     }
+}
+
+// TMA-staged update kernel (complex64 plans, correction form u += e): the
+// same mix, inverse FFT and update as k_upd, in a persistent CTA that walks
+// over tiles of P grid points.  The copy engine brings the next tile's rows
+// of X (F*M rows of P complex values) and of u (L*M rows of P doubles) into
+// the second of two shared-memory buffers, as 2D tensor tiles, while the CTA
+// mixes, transforms and updates the current tile; so neither the mix nor the
+// read-modify-write of u waits on a global load.  Full tiles only (N a
+// multiple of P), u and X 16-byte aligned.
+template <int MM>
+__global__ void __launch_bounds__(256) k_upd_tma(const __grid_constant__ CUtensorMap mapX,
+                                                 const __grid_constant__ CUtensorMap mapU, UpdArgs a,
+                                                 UpdTmaGeom t) {
+    typedef float2 C;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ unsigned long long red[32];
+    __shared__ __align__(8) uint64_t full[2];
+    C* Xs[2] = {reinterpret_cast<C*>(smem_raw), reinterpret_cast<C*>(smem_raw + t.xbuf)};
+    double* Us[2] = {reinterpret_cast<double*>(smem_raw + 2 * t.xbuf),
+                     reinterpret_cast<double*>(smem_raw + 2 * t.xbuf + t.ubuf)};
+    C* Z = reinterpret_cast<C*>(smem_raw + 2 * (t.xbuf + t.ubuf));
+    const int P = a.P, HP = P >> 1;
+    const int logP = 31 - __clz(P), logHP = logP - 1;
+    const int L = a.L;
+    const long N = a.N;
+    const C* Pm = reinterpret_cast<const C*>(a.Pm);
+    const int count = blockIdx.x < t.ntiles ? (t.ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+
+    if (threadIdx.x == 0) {
+        mbar_init(&full[0], 1);
+        mbar_init(&full[1], 1);
+        fence_proxy_async();
+    }
+    __syncthreads();
+    // thread 0: the boxes of local tile i into buffer b
+    auto issue = [&](int i, int b) {
+        const int n0 = ((int)blockIdx.x + i * (int)gridDim.x) * P;
+        fence_proxy_async();
+        mbar_arrive_expect_tx(&full[b], t.tile_bytes);
+        for (int k = 0; k < t.xboxes; ++k)
+            tma_load_2d(Xs[b] + (size_t)k * t.xrows * P, &mapX, 2 * n0, k * t.xrows, &full[b]);
+        for (int k = 0; k < t.uboxes; ++k)
+            tma_load_2d(Us[b] + (size_t)k * t.urows * P, &mapU, n0, k * t.urows, &full[b]);
+    };
+    if (count > 0 && threadIdx.x == 0) issue(0, 0);
+
+    const unsigned long long kAbs = 0x7FFFFFFFFFFFFFFFull;
+    unsigned long long emax = 0ull;
+    for (int i = 0; i < count; ++i) {
+        const int b = i & 1;
+        const long n0 = (long)((int)blockIdx.x + i * (int)gridDim.x) * P;
+        // buffer b ^ 1 was last read in iteration i - 1, which ended with a block barrier
+        if (i + 1 < count && threadIdx.x == 0) issue(i + 1, b ^ 1);
+        const bool ok = mbar_wait_bounded(&full[b], (unsigned)((i >> 1) & 1));
+        if (__syncthreads_or(!ok)) {
+            // the copy engine did not deliver within the limit: report it, give
+            // the copies in flight another bounded wait, and leave
+            if (threadIdx.x == 0) atomicExch(t.err, 1);
+            mbar_wait_bounded(&full[b], (unsigned)((i >> 1) & 1));
+            if (i + 1 < count) mbar_wait_bounded(&full[b ^ 1], (unsigned)(((i + 1) >> 1) & 1));
+            return;
+        }
+        // y = P_k x per stored frequency, from the staged rows of X (as k_upd)
+        const C* Xb = Xs[b];
+        for (int idx = threadIdx.x; idx < a.F * HP; idx += blockDim.x) {
+            const int k = idx >> logHP, q = idx & (HP - 1);
+            C xa[MM], xb[MM];
+#pragma unroll
+            for (int j = 0; j < MM; ++j) {
+                const C* src = Xb + ((long)k * MM + j) * P + 2 * q;
+                xa[j] = src[0];
+                xb[j] = src[1];
+            }
+            const C* Pk = Pm + (long)k * MM * MM;
+            const bool realbin = (k == 0) || (2 * k == L);
+            const int pk = digitrev<3>(k, a.logL), pn = digitrev<3>((L - k) & (L - 1), a.logL);
+#pragma unroll
+            for (int m = 0; m < MM; ++m) {
+                C ya = cmake(0.f, 0.f), yb = ya;
+#pragma unroll
+                for (int j = 0; j < MM; ++j) {
+                    const C pm = Pk[m * MM + j];
+                    ya = cfma(pm, xa[j], ya);
+                    yb = cfma(pm, xb[j], yb);
+                }
+                if (realbin) {
+                    ya.y = 0.f;
+                    yb.y = 0.f;
+                }
+                Z[((long)pk * MM + m) * HP + q] = cmake(ya.x - yb.y, ya.y + yb.x);
+                if (!realbin) Z[((long)pn * MM + m) * HP + q] = cmake(ya.x + yb.y, yb.x - ya.y);
+            }
+        }
+        __syncthreads();
+        fft_inv<C, MM, true>(Z, a.logL, logHP, MM * HP, 1, HP, reinterpret_cast<const C*>(a.tw));
+        // u += sinv_l * z from the staged rows of u
+        const double* Ub = Us[b];
+#pragma unroll 4
+        for (int idx = threadIdx.x; idx < L * MM * HP; idx += blockDim.x) {
+            const int q = idx & (HP - 1);
+            const int lm = idx >> logHP;
+            const int l = lm / MM, m = lm - l * MM;
+            const C z = Z[idx];
+            const double sv = a.sinv[l];
+            const double za = to_double(z.x), zb = to_double(z.y);
+            if (l == L - 1) {
+                const unsigned long long ba = bits_of(za) & kAbs, bb = bits_of(zb) & kAbs;
+                emax = ba > emax ? ba : emax;
+                emax = bb > emax ? bb : emax;
+            }
+            double2 v = *reinterpret_cast<const double2*>(Ub + (long)lm * P + 2 * q);
+            v.x = fma(sv, za, v.x);
+            v.y = fma(sv, zb, v.y);
+            *reinterpret_cast<double2*>(a.out + ((long)l * MM + m) * N + n0 + 2 * q) = v;
+        }
+        __syncthreads();
+    }
+    const unsigned long long mx = block_max_bits(emax, red);
+    if (threadIdx.x == 0) a.part[blockIdx.x] = __longlong_as_double((long long)mx) * a.sinv[L - 1];
 }
 
 template <typename R, int MM, int RAD, int DIM, bool GEN>

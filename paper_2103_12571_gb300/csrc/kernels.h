@@ -54,6 +54,17 @@ struct UpdArgs {
     double* part;                // [gridDim.x] max |e| (or |u_new - u_old|) over the last time block
 };
 
+// Geometry of the TMA-staged update kernel (k_upd_tma): per tile, X rows in
+// xboxes boxes of xrows rows, u rows in uboxes boxes of urows rows; two X
+// and two u buffers and the transform buffer Z in dynamic shared memory.
+struct UpdTmaGeom {
+    int ntiles;                  // N / P
+    int xboxes, xrows, uboxes, urows;
+    unsigned tile_bytes;         // bytes the copy engine delivers per tile (whole boxes)
+    unsigned xbuf, ubuf, zbuf;   // bytes of one X buffer, one u buffer and of Z (multiples of 128)
+    int* err;                    // set to 1 if a wait on the copy engine timed out
+};
+
 // Spatial solves of eq. (d2) on the F*M planes X[f][m][:].
 struct SpaceArgs {
     int nx, ny, lognx, logny, planes, M;
@@ -135,6 +146,12 @@ template <typename R> cudaError_t launch_gmres(const GmresArgs& a, void* scratch
 // bytes of Krylov vectors per system (basis of restart + 1 vectors and x)
 size_t gmres_vector_bytes(int restart, long long N, size_t csize);
 template <typename R> cudaError_t launch_upd(const UpdArgs& a, int grid, size_t smem, cudaStream_t st);
+// TMA-staged update (complex64, correction form); maps: X as [F*M rows][2N floats],
+// u as [L*M rows][N doubles] (CUtensorMap, passed by address)
+cudaError_t launch_upd_tma(const void* mapX, const void* mapU, const UpdArgs& a, const UpdTmaGeom& g, int grid,
+                           cudaStream_t st);
+size_t upd_tma_smem(const UpdTmaGeom& g);
+int upd_tma_ctas_per_sm(int M, const UpdTmaGeom& g);
 // shared memory the update kernel needs for these arguments (rsize = bytes per real of the transform)
 size_t upd_smem(const UpdArgs& a, size_t rsize);
 template <typename R> cudaError_t launch_space_1d(const SpaceArgs& a, cudaStream_t st);

@@ -293,6 +293,56 @@ def test_unaligned_buffers_take_the_scalar_path():
     assert torch.equal(ua, ub)
 
 
+@pytest.mark.parametrize("prob", [workloads.problem(2, 256, 256, nu=0.05, order=2, M=3, L=64, T=0.5),
+                                  workloads.problem(1, 1024, cx=1.0, order=4, M=3, L=128, T=0.5)],
+                         ids=["heat2d_256_L64", "adv1d_1024_L128"])
+def test_tma_staged_update_equals_plain_update(prob):
+    """A complex64 plan built with update_kernel = AC_UPDATE_TMA updates
+    u += e with the TMA-staged kernel (2D tensor tiles of X and u copied into
+    shared memory, double-buffered) when u is 16-byte aligned, and with the
+    plain kernel otherwise.  The arithmetic is the same, so the iterates must
+    agree bit for bit with the plain plan's and with its own unaligned
+    fallback.  The second case needs two boxes per tile for the rows of u
+    (L*M = 384 > 256)."""
+    torch = torch_cuda()
+    from paper_2103_12571_gb300.api import Plan
+    L, M = prob["L"], prob["M"]
+    N = prob["nx"] * prob["ny"]
+    rng = np.random.default_rng(13)
+    u0 = to_dev(torch, rng.standard_normal(N))
+    tma = Plan(prob, precision="c64", update_kernel="tma")
+    plain = Plan(prob, precision="c64")
+    assert tma.info()["update_kernel"] == 1 and tma.info()["update_tile_tma"] >= 8
+    assert plain.info()["update_kernel"] == 0
+    ua = to_dev(torch, rng.standard_normal((L, M, N)))
+    uc = ua.clone()
+    big = torch.empty(L * M * N + 1, dtype=torch.float64, device="cuda")
+    ub = big[1:].view(L, M, N)          # 8-byte aligned only: the plain kernel
+    ub.copy_(ua)
+    for _ in range(3):
+        ra = tma.richardson_step(2e-3, u0, ua, want_residual=True)
+        rb = tma.richardson_step(2e-3, u0, ub, want_residual=True)
+        rc = plain.richardson_step(2e-3, u0, uc, want_residual=True)
+        assert ra == rb == rc
+    torch.cuda.synchronize()
+    assert torch.equal(ua, ub) and torch.equal(ua, uc)
+
+
+def test_tma_staged_update_solve_matches_oracle():
+    """A whole mixed-form solve with the TMA-staged update kernel against the
+    sequential oracle (1e-10)."""
+    torch = torch_cuda()
+    from paper_2103_12571_gb300.api import Plan
+    prob = SMALL[5]
+    Q, A, dT = oracle_setup(prob)
+    u0 = np.random.default_rng(14).standard_normal(operators.n_points(prob))
+    ref = sequential.sequential_solve(A, Q, dT, prob["L"], u0)
+    plan = Plan(prob, precision="c64", alpha="mixed", max_iter=40, update_kernel="tma")
+    assert plan.info()["update_kernel"] == 1
+    u, st = plan.solve(to_dev(torch, u0), tol=1e-13, raise_on_fail=False)
+    assert rel2(u.cpu().numpy(), ref) < 1e-10, st
+
+
 # ------------------------------------------------- eq. (Riteration) as printed
 @pytest.mark.parametrize("prob", [SMALL[0], SMALL[4], SMALL[6]], ids=ids)
 def test_paper_form_iterates_match_oracle(prob):
