@@ -149,7 +149,11 @@ def kernel_counts(prob, csize, taps):
     """Algorithmic flops and HBM bytes per launch of each kernel kind of one
     iteration (the library's profiler names).  FFTs of length n count
     5 n log2 n flops per complex transform (2.5 n log2 n for a real one);
-    a complex multiply-add counts 8, the pointwise shifted division 6.
+    a complex multiply-add counts 8.  The pointwise shifted division
+    v / (1 - mu sigma_x - mu sigma_y), with the products mu sigma tabulated
+    per axis, counts 15: 3 to form the denominator, 3 for its squared
+    modulus, 1 reciprocal, 6 for the product with its conjugate and 2 to
+    scale.
     Bytes: each array read or written once per launch."""
     L, M = prob["L"], prob["M"]
     nx, ny = prob["nx"], prob["ny"] if prob["dim"] == 2 else 1
@@ -164,8 +168,8 @@ def kernel_counts(prob, csize, taps):
         "resid_tfft_mix": {"flops": D * fp64_flops_per_dof(M, taps) + tfft + mix,
                            "bytes": 8.0 * D + P * csize, "points": P},
         "space_rows": {"flops": P * 5.0 * lg(nx), "bytes": 2.0 * P * csize, "points": P},
-        "space_cols": {"flops": P * (10.0 * lg(ny) + 6.0), "bytes": 2.0 * P * csize, "points": P},
-        "spatial_solve": {"flops": P * (10.0 * lg(N) + 6.0), "bytes": 2.0 * P * csize, "points": P},
+        "space_cols": {"flops": P * (10.0 * lg(ny) + 15.0), "bytes": 2.0 * P * csize, "points": P},
+        "spatial_solve": {"flops": P * (10.0 * lg(N) + 15.0), "bytes": 2.0 * P * csize, "points": P},
         "mix_tifft_update": {"flops": mix + tfft + 2.0 * D, "bytes": P * csize + 16.0 * D, "points": P},
     }
 

@@ -218,6 +218,10 @@ static cudaError_t upload_c(const ac_plan* p, void* dst, const cd* src, size_t n
     return cudaMemcpyAsync(dst, tmp.data(), tmp.size() * sizeof(float), cudaMemcpyHostToDevice, st);
 }
 
+// The spatial FFT solves return N times the solution (unnormalised inverse
+// transforms); the back transforms after them absorb 1/N.
+static double space_scale(const ac_plan* p) { return p->spatial_path <= 2 ? 1.0 / (double)p->N : 1.0; }
+
 // Alpha-dependent tables (ac::alpha_tables): qs, s, the residual-norm
 // weights, sinv (FP64 / float pairs) and the per-frequency Sinv, P, dT mu
 // (transform precision).
@@ -225,7 +229,7 @@ static int ensure_tables(ac_plan* p, double alpha, int transposed, double wscale
     if (alpha == p->cur_alpha && transposed == p->cur_transposed && wscale == p->cur_wscale) return AC_OK;
     if (!(alpha > 0.0) || !(alpha < 1.0)) return fail(AC_ERR_INVALID_ARG, "alpha must be in (0,1), got %g", alpha);
     ac::AlphaTables T;
-    if (!ac::alpha_tables(p->M, p->L, p->dT, p->Q, p->t, alpha, transposed != 0, wscale, &T))
+    if (!ac::alpha_tables(p->M, p->L, p->dT, p->Q, p->t, alpha, transposed != 0, wscale, space_scale(p), &T))
         return fail(AC_ERR_NOT_DIAGONALIZABLE, "Q G_l^{-1} not diagonalisable for alpha=%g (cond %g)", alpha,
                     T.worst_cond);
     CK(cudaMemcpyAsync(p->d_qs, T.qs.data(), T.qs.size() * sizeof(double), cudaMemcpyHostToDevice, st));
@@ -828,6 +832,7 @@ static int ensure_seq_tables(ac_plan* p, cudaStream_t st) {
     const double c = ac::eig_small(M, B.data(), lam.data(), S.data(), Sinv.data());
     if (c < 0 || c > 1e10) return fail(AC_ERR_NOT_DIAGONALIZABLE, "Q is not diagonalisable (cond %g)", c);
     for (auto& v : lam) v *= p->dT;
+    for (auto& v : S) v *= space_scale(p);   // the back-mix absorbs the FFT solves' factor N
     cudaError_t e = cudaMalloc((void**)&p->d_seq_S, sizeof(cd) * M * M);
     if (e == cudaSuccess) e = cudaMalloc((void**)&p->d_seq_Sinv, sizeof(cd) * M * M);
     if (e == cudaSuccess) e = cudaMalloc(&p->d_seq_mu, (size_t)M * p->csize);

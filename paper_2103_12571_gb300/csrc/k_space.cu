@@ -4,7 +4,10 @@
 // x^2 = IFFT( FFT(x^1) / (1 - dT mu sigma(k)) ), sigma the stencil symbol.
 // Forward FFTs leave the spectrum in digit-reversed order and the inverse
 // FFTs take it back from there, so no reordering pass is needed: the
-// division only needs the true wavenumber of each slot (digitrev).
+// division only needs the true wavenumber of each slot (digitrev).  The
+// inverse transforms are not normalised: the planes come back multiplied by
+// N = nx ny, and the back transform that follows (the update kernel's
+// unscaling table, the sequential stepping's back-mix) absorbs 1/N.
 //
 // Radix plans (template SB: stages of up to 2^SB points).  Complex64
 // transforms use radix 8 (register pressure).  Complex128 transforms run on
@@ -32,15 +35,19 @@ __device__ __forceinline__ double rcp_newton(double x, double one) {
 }
 __device__ __forceinline__ float rcp_newton(float x, float) { return __frcp_rn(x); }
 
-// v / (1 - m) with m = mu sigma: multiply by conj(1 - m) / |1 - m|^2
-// (|1 - m| >= 1 whenever Re(mu sigma) <= 0; in any case far from 0 here).
+// v / den: multiply by conj(den) / |den|^2 (den = 1 - mu sigma, with
+// |den| >= 1 whenever Re(mu sigma) <= 0; in any case far from 0 here).
+template <typename C, typename R>
+__device__ __forceinline__ C div_by(C v, C den, R one) {
+    const R inv = rcp_newton(fma(den.x, den.x, den.y * den.y), one);
+    return cscale(cmulc(v, den), inv);
+}
 template <typename C, typename R>
 __device__ __forceinline__ C div_one_minus(C v, C m, R one) {
     C den;
     den.x = one - m.x;
     den.y = -m.y;
-    const R inv = rcp_newton(fma(den.x, den.x, den.y * den.y), one);
-    return cscale(cmulc(v, den), inv);
+    return div_by(v, den, one);
 }
 
 // One CTA per 1D plane held in shared memory.
@@ -64,8 +71,7 @@ __global__ void __launch_bounds__(512) k_space_1d(SpaceArgs a) {
     }
     __syncthreads();
     fft_inv<C, 1, false, SB>(d, logn, 0, 1, 0, 0, tw);
-    const R sc = (R)1 / (R)n;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] = cscale(d[i], sc);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] = d[i];   // times n (not normalised)
 }
 
 // One CTA per 2D plane held in shared memory (row FFTs, column FFTs, divide,
@@ -96,12 +102,11 @@ __global__ void __launch_bounds__(512) k_space_2d_small(SpaceArgs a) {
     __syncthreads();
     fft_inv<C, 1, true, SBY>(d, ly, lx, nx, 1, 0, twy);
     fft_inv<C, 1, false, SBX>(d, lx, ly, 1, nx, 0, twx);
-    const R sc = (R)1 / (R)N;
-    for (long i = threadIdx.x; i < N; i += blockDim.x) x[i] = cscale(d[i], sc);
+    for (long i = threadIdx.x; i < N; i += blockDim.x) x[i] = d[i];   // times N (not normalised)
 }
 
 // Row pass of the three-pass 2D path: rows_per_block contiguous rows of length
-// nx; forward FFT, or inverse FFT with the 1/(nx ny) normalisation.
+// nx; forward FFT, or inverse FFT (not normalised).
 template <typename R, int SBX>
 __global__ void __launch_bounds__(256) k_space_rows(SpaceArgs a, int inverse) {
     typedef typename Cx<R>::T C;
@@ -127,19 +132,18 @@ __global__ void __launch_bounds__(256) k_space_rows(SpaceArgs a, int inverse) {
         }
     } else {
         fft_inv<C, 1, true, SBX>(d, a.lognx, logr, ld, 1, 0, tw);
-        const R sc = (R)1 / ((R)nx * (R)a.ny);
         for (long i = threadIdx.x; i < cnt; i += blockDim.x) {
             const int row = (int)(i >> a.lognx), ix = (int)(i & (nx - 1));
-            x[i] = cscale(d[ix * ld + row], sc);
+            x[i] = d[ix * ld + row];
         }
     }
 }
 
 // Column pass: a tile of W consecutive x slots (digit-reversed order of the
 // row pass's plan SBX) times all ny rows of one plane; forward FFT along y,
-// divide, inverse FFT along y.  The products mu sigma_x and mu sigma_y of
-// the tile's x slots and of every y slot are formed once per CTA, so the
-// division needs only their sum per point.
+// divide, inverse FFT along y.  1 - mu sigma_x of the tile's x slots and
+// mu sigma_y of every y slot are formed once per CTA, so the denominator of a
+// point is one complex subtraction.
 template <typename R, int SBX, int SBY>
 __global__ void __launch_bounds__(256) k_space_cols(SpaceArgs a) {
     typedef typename Cx<R>::T C;
@@ -159,17 +163,20 @@ __global__ void __launch_bounds__(256) k_space_cols(SpaceArgs a) {
     const C mu = reinterpret_cast<const C*>(a.mu_dT)[plane];
     const C* sx = reinterpret_cast<const C*>(a.sig_x);
     const C* sy = reinterpret_cast<const C*>(a.sig_y);
-    C* mx = d + cnt;                  // W entries: mu sigma_x of this tile's x slots
-    C* my = mx + W;                   // ny entries: mu sigma_y per y slot
-    for (int i = threadIdx.x; i < W; i += blockDim.x) mx[i] = cmul(mu, sx[slot_freq<SBX>(c0 + i, a.lognx)]);
-    for (int i = threadIdx.x; i < ny; i += blockDim.x) my[i] = cmul(mu, sy[slot_freq<SBY>(i, a.logny)]);
-    __syncthreads();
     const C* twy = reinterpret_cast<const C*>(a.tw_y);
     const R one = twy[0].x;
+    C* mx = d + cnt;                  // W entries: 1 - mu sigma_x of this tile's x slots
+    C* my = mx + W;                   // ny entries: mu sigma_y per y slot
+    for (int i = threadIdx.x; i < W; i += blockDim.x) {
+        const C m = cmul(mu, sx[slot_freq<SBX>(c0 + i, a.lognx)]);
+        mx[i] = cmake(one - m.x, -m.y);
+    }
+    for (int i = threadIdx.x; i < ny; i += blockDim.x) my[i] = cmul(mu, sy[slot_freq<SBY>(i, a.logny)]);
+    __syncthreads();
     fft_fwd<C, 1, true, SBY>(d, a.logny, logW, W, 1, 0, twy);
     for (long i = threadIdx.x; i < cnt; i += blockDim.x) {
         const int ys = (int)(i >> logW), w = (int)(i & (W - 1));
-        d[i] = div_one_minus(d[i], cadd(mx[w], my[ys]), one);
+        d[i] = div_by(d[i], csub(mx[w], my[ys]), one);
     }
     __syncthreads();
     fft_inv<C, 1, true, SBY>(d, a.logny, logW, W, 1, 0, twy);

@@ -146,7 +146,7 @@ int run(const ac_problem* prob, int M, int L, double dT, double alpha, const dou
     ac::axis_symbol(nx, sten.tx, sx.data());
     if (prob->dim == 2) ac::axis_symbol(ny, sten.ty, sy.data());
     ac::AlphaTables T;
-    if (!ac::alpha_tables(M, L, dT, Q, t, alpha, false, 1.0, &T))
+    if (!ac::alpha_tables(M, L, dT, Q, t, alpha, false, 1.0, 1.0 / (double)N, &T))
         return nfail(AC_ERR_NOT_DIAGONALIZABLE, "Q G_l^{-1} not diagonalisable");
 
     cudaError_t ce = cudaSuccess;

@@ -474,7 +474,7 @@ const char* plan_shape(const ac_problem& prob, int M, int L, int precision, int 
 }
 
 bool alpha_tables(int M, int L, double dT, const double* Q, const double* t, double alpha, bool transposed,
-                  double wscale, AlphaTables* o) {
+                  double wscale, double space_scale, AlphaTables* o) {
     const int F = L / 2 + 1;
     o->qs.assign((size_t)L * M * M, 0.0);
     o->s.assign(L, 0.0);
@@ -482,7 +482,7 @@ bool alpha_tables(int M, int L, double dT, const double* Q, const double* t, dou
     o->wnorm.assign(2 * (size_t)L, 0.f);
     for (int l = 0; l < L; ++l) {
         o->s[l] = (l == 0) ? 1.0 : std::pow(alpha, (double)l / L);
-        o->sinv[l] = ((l == 0) ? 1.0 : std::pow(alpha, -(double)l / L)) / L;
+        o->sinv[l] = ((l == 0) ? 1.0 : std::pow(alpha, -(double)l / L)) / L * space_scale;
         const double w = 1048576.0 / (o->s[l] * wscale);   // 2^20: the kernels' norm prescale
         const float wh = (float)w;
         o->wnorm[2 * l] = wh;

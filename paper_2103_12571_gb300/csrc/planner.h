@@ -68,7 +68,8 @@ const char* plan_shape(const ac_problem& prob, int M, int L, int precision, int 
 
 // The alpha-dependent tables of one preconditioner (Lemma 1, eq. (QGL)):
 // per step l: s_l = alpha^{l/L}, qs_l = s_l dT Q (Q^T if transposed),
-// sinv_l = alpha^{-l/L} / L, the residual-norm weight 2^20 / (s_l w_scale)
+// sinv_l = alpha^{-l/L} / L times space_scale (1/N after the unnormalised
+// spatial FFT solves, 1 after Krylov solves), the residual-norm weight 2^20 / (s_l w_scale)
 // as a float pair; per stored frequency f: dT mu_{f,m}, S_f^{-1} and
 // P_f = G_f^{-1} S_f.  Returns false (with worst_cond set) if some S_f is
 // ill-conditioned (cond > 1e10) or the eigen-decomposition failed.
@@ -79,6 +80,6 @@ struct AlphaTables {
     double worst_cond;
 };
 bool alpha_tables(int M, int L, double dT, const double* Q, const double* t, double alpha, bool transposed,
-                  double wscale, AlphaTables* out);
+                  double wscale, double space_scale, AlphaTables* out);
 
 }  // namespace ac
