@@ -85,7 +85,7 @@ extern "C" {
  * The stencil radius is at most 3.  dim = 1 ignores ny, ly, cy. */
 typedef struct {
     int dim;          /* 1 or 2                                     */
-    int nx, ny;       /* grid points per axis (powers of two for AC_INNER_FFT) */
+    int nx, ny;       /* grid points per axis (prime factors 2, 3, 5, 7 only for AC_INNER_FFT) */
     double lx, ly;    /* box lengths                                */
     double nu;        /* diffusion coefficient                      */
     double cx, cy;    /* advection velocity                         */
@@ -129,7 +129,8 @@ typedef struct {
     int N, M, L, F;                   /* F = L/2 + 1 stored time frequencies            */
     int tile_fwd, tile_upd;           /* grid points per CTA in the time kernels        */
     int spatial_path;                 /* 0: 1D one CTA per plane, 1: 2D one CTA per plane, 2: 2D three passes,
-                                         3: BiCGStab, 4: GMRES                                               */
+                                         3: BiCGStab, 4: GMRES; 5: 1D mixed-radix FFT (sizes that are not
+                                         powers of two), one CTA per plane, 6: 2D mixed-radix three passes */
     long long workspace_bytes;        /* device memory owned by the plan               */
     long long launches;               /* kernels launched by this plan so far          */
     int update_kernel;                /* AC_UPDATE_TMA if the TMA-staged update kernel is in use
@@ -147,9 +148,10 @@ typedef struct ac_plan ac_plan;
  * M >= 1 (<= 4), L a power of two (2..1024) with L*M small enough for the
  * shared-memory time transform, dT > 0, a supported stencil scheme (see
  * ac_problem).  precision: AC_C128 or AC_C64.  inner: AC_INNER_FFT needs
- * power-of-two nx (and ny) and a 1D grid of at most 160 KB of transform values
- * per plane; AC_INNER_BICGSTAB and AC_INNER_GMRES take any grid with at least
- * 2 * radius + 1 points per axis.  Writes *out.
+ * nx (and ny) without prime factors above 7 and a 1D plane of at most 160 KB of
+ * transform values (powers of two; 100 KB for other sizes, whose Stockham
+ * transforms keep two copies); AC_INNER_BICGSTAB and AC_INNER_GMRES take any
+ * grid with at least 2 * radius + 1 points per axis.  Writes *out.
  * Errors: AC_ERR_INVALID_ARG for unsupported sizes or schemes, AC_ERR_CUDA. */
 int ac_setup(const ac_problem* prob, int M, int L, double dT,
              const ac_alpha_schedule* sched, int precision, int inner,
@@ -286,8 +288,9 @@ int ac_grad_params(ac_plan* plan, const double* u, const double* lam,
  * are uploaded on every call from pageable host memory, so the host waits
  * until the work queued before the call on `stream` has finished; the
  * kernels are then queued without further waits.
- *   prob, M, L, dT: as for ac_setup (FFT inner solve, power-of-two grid, L a
- *     power of two in 2..1024, M in 1..4); precision: AC_C128 or AC_C64.
+ *   prob, M, L, dT: as for ac_setup (FFT inner solve, grid sizes with prime
+ *     factors 2, 3, 5, 7 only, L a power of two in 2..1024, M in 1..4);
+ *     precision: AC_C128 or AC_C64.
  *   alpha in (0,1).  r, e: device, L*M*N doubles (may be the same buffer).
  * The first call on a device looks up the array's device address (once per
  * device, with that device current); make that first call before any stream

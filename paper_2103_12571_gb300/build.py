@@ -15,7 +15,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libalphacirc.so")
-SOURCES = ["api.cu", "k_fwd_f32.cu", "k_fwd_f64.cu", "k_upd.cu", "k_space.cu", "k_misc.cu", "k_krylov.cu",
+SOURCES = ["api.cu", "k_fwd_f32.cu", "k_fwd_f64.cu", "k_upd.cu", "k_space.cu", "k_space_mr.cu", "k_misc.cu",
+           "k_krylov.cu",
            "noalloc.cu", "planner.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -75,6 +75,7 @@ struct ac_plan {
     int precision, inner, device;
     int spatial_path;
     int rows_per_block, cols_per_block;
+    ac::FftRadices rx, ry;   // radix plans of the mixed-radix FFT paths (5, 6)
     size_t csize;  // bytes per complex of the transform type
     // host data
     double t[8], Q[64];
@@ -220,7 +221,8 @@ static cudaError_t upload_c(const ac_plan* p, void* dst, const cd* src, size_t n
 
 // The spatial FFT solves return N times the solution (unnormalised inverse
 // transforms); the back transforms after them absorb 1/N.
-static double space_scale(const ac_plan* p) { return p->spatial_path <= 2 ? 1.0 / (double)p->N : 1.0; }
+static bool krylov_path(const ac_plan* p) { return p->spatial_path == 3 || p->spatial_path == 4; }
+static double space_scale(const ac_plan* p) { return krylov_path(p) ? 1.0 : 1.0 / (double)p->N; }
 
 // Alpha-dependent tables (ac::alpha_tables): qs, s, the residual-norm
 // weights, sinv (FP64 / float pairs) and the per-frequency Sinv, P, dT mu
@@ -287,6 +289,8 @@ static int run_spatial(ac_plan* p, void* X, const void* mu_dT, int planes, int t
     sa.tw_y = p->tw_y;
     sa.rows_per_block = p->rows_per_block;
     sa.cols_per_block = p->cols_per_block;
+    sa.rx = p->rx;
+    sa.ry = p->ry;
     if (p->spatial_path == 0) {
         CK(ac::launch_space_1d<R>(sa, st));
         p->launches++;
@@ -306,6 +310,24 @@ static int run_spatial(ac_plan* p, void* X, const void* mu_dT, int planes, int t
         {
             ProfScope ps(p, pp ? KK_SPACE_ROWS : -1, st);
             CK(ac::launch_space_rows<R>(sa, 1, st));
+        }
+        p->launches += 3;
+    } else if (p->spatial_path == 5) {
+        CK(ac::launch_space_mr_1d<R>(sa, st));
+        p->launches++;
+    } else if (p->spatial_path == 6) {
+        const bool pp = prof_passes && p->prof;
+        {
+            ProfScope ps(p, pp ? KK_SPACE_ROWS : -1, st);
+            CK(ac::launch_space_mr_rows<R>(sa, 0, st));
+        }
+        {
+            ProfScope ps(p, pp ? KK_SPACE_COLS : -1, st);
+            CK(ac::launch_space_mr_cols<R>(sa, st));
+        }
+        {
+            ProfScope ps(p, pp ? KK_SPACE_ROWS : -1, st);
+            CK(ac::launch_space_mr_rows<R>(sa, 1, st));
         }
         p->launches += 3;
     } else if (p->spatial_path == 3) {
@@ -760,7 +782,7 @@ static int richardson_loop(ac_plan* p, const double* u0, const double* b, int b_
         rc = precond_a(p, u, u0, b, b_rev, transposed, st, true, 0, !speculate);
         if (rc) return rc;
         CK(cudaEventSynchronize(p->ev_res));
-        if (k > 0 && p->spatial_path >= 3) S->inner_iters[k - 1] = inner_summary(p, &S->inner_failed[k - 1]);
+        if (k > 0 && krylov_path(p)) S->inner_iters[k - 1] = inner_summary(p, &S->inner_failed[k - 1]);
         double s = 0.0;
         for (int i = 0; i < p->grid; ++i) s += p->h_part_fwd[i];
         const double res = std::sqrt(s) * (wscale / ac::kNormPrescale) / wn2;
@@ -1042,6 +1064,8 @@ int ac_setup(const ac_problem* prob, int M, int L, double dT, const ac_alpha_sch
     p->spatial_path = shape.spatial_path;
     p->rows_per_block = shape.rows_per_block;
     p->cols_per_block = shape.cols_per_block;
+    p->rx = shape.rx;
+    p->ry = shape.ry;
     p->P = shape.P;
     p->grid = shape.grid;
     p->P_upd = shape.P_upd;
@@ -1092,7 +1116,7 @@ int ac_setup(const ac_problem* prob, int M, int L, double dT, const ac_alpha_sch
     if (e == cudaSuccess) e = cudaMallocHost((void**)&p->h_part_fwd, sizeof(double) * p->grid);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&p->h_part_upd, sizeof(double) * std::max(p->grid_upd, 8 * 152));
     if (e == cudaSuccess) e = cudaMallocHost((void**)&p->h_part_d, sizeof(double) * p->part_d_len);
-    if (e == cudaSuccess && p->spatial_path >= 3) e = cudaMallocHost((void**)&p->h_iters, sizeof(int) * F * M);
+    if (e == cudaSuccess && krylov_path(p)) e = cudaMallocHost((void**)&p->h_iters, sizeof(int) * F * M);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_res, cudaEventDisableTiming);  // spin: low latency
     if (e != cudaSuccess) {
         int rc = fail(AC_ERR_CUDA, "allocation failed: %s", cudaGetErrorString(e));

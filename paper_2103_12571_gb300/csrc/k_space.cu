@@ -22,34 +22,6 @@
 
 namespace ac {
 
-// Reciprocal of a positive double: a float seed (FP32 reciprocal, converted
-// on the integer pipe) and two Newton-Raphson steps y <- y + y (1 - x y),
-// each of which doubles the number of correct bits (24 -> 48 -> full FP64).
-// Valid for x in the normal float range, which the shifted symbols
-// |1 - mu sigma|^2 of the solver stay in.
-__device__ __forceinline__ double rcp_newton(double x, double one) {
-    double y = f2d_int(__frcp_rn(d2f_int(x)));
-    y = fma(y, fma(-x, y, one), y);
-    y = fma(y, fma(-x, y, one), y);
-    return y;
-}
-__device__ __forceinline__ float rcp_newton(float x, float) { return __frcp_rn(x); }
-
-// v / den: multiply by conj(den) / |den|^2 (den = 1 - mu sigma, with
-// |den| >= 1 whenever Re(mu sigma) <= 0; in any case far from 0 here).
-template <typename C, typename R>
-__device__ __forceinline__ C div_by(C v, C den, R one) {
-    const R inv = rcp_newton(fma(den.x, den.x, den.y * den.y), one);
-    return cscale(cmulc(v, den), inv);
-}
-template <typename C, typename R>
-__device__ __forceinline__ C div_one_minus(C v, C m, R one) {
-    C den;
-    den.x = one - m.x;
-    den.y = -m.y;
-    return div_by(v, den, one);
-}
-
 // One CTA per 1D plane held in shared memory.
 template <typename R, int SB>
 __global__ void __launch_bounds__(512) k_space_1d(SpaceArgs a) {

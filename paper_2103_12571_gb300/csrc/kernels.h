@@ -3,6 +3,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "radices.h"
+
 namespace ac {
 
 // Off-centre stencil offsets in the order the kernels visit them (radius 1,
@@ -72,9 +74,10 @@ struct SpaceArgs {
     const void* mu_dT;           // [F*M] complex dT * mu_{f,m}
     const void* sig_x;           // [nx] complex symbol of the x part of A
     const void* sig_y;           // [ny] complex symbol of the y part (2D)
-    const void* tw_x;            // nx/2 twiddles
-    const void* tw_y;            // ny/2 twiddles
+    const void* tw_x;            // [nx] twiddles exp(-2 pi i k / nx), k < nx
+    const void* tw_y;            // [ny] twiddles
     int rows_per_block, cols_per_block;
+    FftRadices rx, ry;           // radix plans of the mixed-radix (non-power-of-two) solves
 };
 
 // BiCGStab on (I - dT mu A) x = X-plane with the stencil, tolerance tau.
@@ -158,6 +161,14 @@ template <typename R> cudaError_t launch_space_1d(const SpaceArgs& a, cudaStream
 template <typename R> cudaError_t launch_space_2d_small(const SpaceArgs& a, cudaStream_t st);
 template <typename R> cudaError_t launch_space_rows(const SpaceArgs& a, int inverse, cudaStream_t st);
 template <typename R> cudaError_t launch_space_cols(const SpaceArgs& a, cudaStream_t st);
+// Mixed-radix solves (grid sizes with prime factors 2, 3, 5, 7 only): one CTA
+// per 1D plane, and the row / column passes of the three-pass 2D solve.
+template <typename R> cudaError_t launch_space_mr_1d(const SpaceArgs& a, cudaStream_t st);
+template <typename R> cudaError_t launch_space_mr_rows(const SpaceArgs& a, int inverse, cudaStream_t st);
+template <typename R> cudaError_t launch_space_mr_cols(const SpaceArgs& a, cudaStream_t st);
+// Shared memory of a mixed-radix pass (0: 1D plane of n, 1: batch rows of n,
+// 2: batch columns of ny) for complex values of csize bytes.
+size_t space_mr_smem(int pass, int n, int batch, int ny, size_t csize);
 template <typename R> cudaError_t launch_bicgstab(const BicgArgs& a, void* scratch, cudaStream_t st);
 cudaError_t launch_apply(const ApplyArgs& a, cudaStream_t st);
 cudaError_t launch_grad(const GradArgs& a, int grid, cudaStream_t st);

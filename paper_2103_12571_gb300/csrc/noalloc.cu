@@ -215,12 +215,20 @@ int run(const ac_problem* prob, int M, int L, double dT, double alpha, const dou
     sa.tw_y = base + otwy;
     sa.rows_per_block = sh.rows_per_block;
     sa.cols_per_block = sh.cols_per_block;
+    sa.rx = sh.rx;
+    sa.ry = sh.ry;
     if (sh.spatial_path == 0) chk(ac::launch_space_1d<R>(sa, st));
     else if (sh.spatial_path == 1) chk(ac::launch_space_2d_small<R>(sa, st));
-    else {
+    else if (sh.spatial_path == 2) {
         chk(ac::launch_space_rows<R>(sa, 0, st));
         chk(ac::launch_space_cols<R>(sa, st));
         chk(ac::launch_space_rows<R>(sa, 1, st));
+    } else if (sh.spatial_path == 5) {
+        chk(ac::launch_space_mr_1d<R>(sa, st));
+    } else {
+        chk(ac::launch_space_mr_rows<R>(sa, 0, st));
+        chk(ac::launch_space_mr_cols<R>(sa, st));
+        chk(ac::launch_space_mr_rows<R>(sa, 1, st));
     }
 
     ac::UpdArgs ua{};
@@ -251,8 +259,8 @@ extern "C" int ac_precond_solve_noalloc(const ac_problem* prob, int M, int L, do
     if (prob->upwind ? (prob->order < 1 || prob->order > 5) : (prob->order != 2 && prob->order != 4 && prob->order != 6))
         return nfail(AC_ERR_INVALID_ARG, "order must be 2, 4 or 6 (centred) or 1..5 (upwind)");
     const int ny = prob->dim == 2 ? prob->ny : 1;
-    if (prob->nx < 2 || (prob->dim == 2 && ny < 2) || !pow2(prob->nx) || !pow2(ny))
-        return nfail(AC_ERR_INVALID_ARG, "grid sizes must be powers of two >= 2");
+    if (prob->nx < 2 || (prob->dim == 2 && ny < 2))
+        return nfail(AC_ERR_INVALID_ARG, "grid sizes must be >= 2");
     if (M < 1 || M > 4) return nfail(AC_ERR_INVALID_ARG, "M must be 1..4");
     if (!pow2(L) || L < 2 || L > 1024) return nfail(AC_ERR_INVALID_ARG, "L must be a power of two in 2..1024");
     if (!(dT > 0)) return nfail(AC_ERR_INVALID_ARG, "dT must be positive");

@@ -419,6 +419,20 @@ void twiddles(int n, std::vector<cd>& tw) {
 
 static bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 
+bool fft_radices(int n, FftRadices* o) {
+    static const int pref[6] = {8, 7, 5, 4, 3, 2};
+    o->ns = 0;
+    if (n < 1) return false;
+    for (int i = 0; i < 6; ++i) {
+        while (n % pref[i] == 0) {
+            if (o->ns == 15) return false;
+            o->r[o->ns++] = pref[i];
+            n /= pref[i];
+        }
+    }
+    return n == 1;
+}
+
 const char* plan_shape(const ac_problem& prob, int M, int L, int precision, int inner, int rad, PlanShape* o) {
     const int nx = prob.nx, ny = prob.dim == 2 ? prob.ny : 1;
     const long long N = (long long)nx * ny;
@@ -426,8 +440,30 @@ const char* plan_shape(const ac_problem& prob, int M, int L, int precision, int 
     *o = PlanShape{};
     o->rows_per_block = 1;
     o->cols_per_block = 1;
-    if (inner == AC_INNER_FFT) {
-        if (!is_pow2(nx) || !is_pow2(ny)) return "the FFT inner solver needs power-of-two grid sizes";
+    if (inner == AC_INNER_FFT && (!is_pow2(nx) || !is_pow2(ny))) {
+        // Mixed-radix Stockham transforms between two shared-memory buffers.
+        if (!fft_radices(nx, &o->rx) || !fft_radices(ny, &o->ry))
+            return "the FFT inner solver needs grid sizes whose prime factors are 2, 3, 5 and 7";
+        const size_t limit = 200 * 1024;
+        if (prob.dim == 1) {
+            if (2 * (size_t)nx * cs > limit) return "1D grid too large for the one-CTA mixed-radix FFT solve";
+            o->spatial_path = 5;
+        } else {
+            o->spatial_path = 6;
+            // rows: about 64 KB per CTA (three CTAs per SM); columns: 8 (complex64)
+            // or 4 (complex128) per CTA, fewer if a tile would not fit
+            int rpb = (int)(65536 / (2 * (size_t)nx * cs));
+            if (rpb < 1) rpb = 1;
+            if (rpb > ny) rpb = ny;
+            o->rows_per_block = rpb;
+            int W = cs == 16 ? 4 : 8;
+            if (W > nx) W = nx;
+            while (W > 1 && (2 * (size_t)ny * W + W + ny) * cs > limit) W >>= 1;
+            o->cols_per_block = W;
+            if (2 * (size_t)nx * cs > limit || (2 * (size_t)ny * W + W + ny) * cs > limit)
+                return "2D grid too large for the three-pass mixed-radix FFT solve";
+        }
+    } else if (inner == AC_INNER_FFT) {
         if (prob.dim == 1) {
             if ((size_t)nx * cs > 160 * 1024) return "1D grid too large for the one-CTA FFT solve";
             o->spatial_path = 0;

@@ -6,6 +6,7 @@
 #include <vector>
 
 #include "alphacirc.h"
+#include "radices.h"
 
 namespace ac {
 
@@ -56,11 +57,18 @@ void twiddles(int n, std::vector<cd>& tw);
 // the same launches.
 struct PlanShape {
     int spatial_path;               // 0: 1D FFT, one CTA per plane; 1: 2D FFT, one CTA per plane;
-                                    // 2: 2D FFT in three passes; 3: BiCGStab; 4: GMRES
+                                    // 2: 2D FFT in three passes; 3: BiCGStab; 4: GMRES;
+                                    // 5: 1D mixed-radix FFT, one CTA per plane; 6: 2D mixed-radix
+                                    // FFT in three passes (5, 6: sizes that are not powers of two)
     int rows_per_block, cols_per_block;   // three-pass tiles
+    FftRadices rx, ry;              // radix plans of paths 5 and 6
     int P, grid;                    // residual kernel: grid points per CTA, CTAs
     int P_upd, grid_upd;            // update kernel: grid points per CTA, CTAs
 };
+// Radix plan of a mixed-radix FFT of length n (radices 8, 7, 5, 4, 3, 2, in
+// that order of preference).  False if n has a prime factor above 7.
+bool fft_radices(int n, FftRadices* out);
+
 // Null on success, else a message naming the unsupported size.  rad: the
 // stencil radius (Krylov paths need 2 rad + 1 points per axis).
 const char* plan_shape(const ac_problem& prob, int M, int L, int precision, int inner, int rad,

@@ -96,13 +96,13 @@ def _advection(dim, N, order, M, L, T):
     return prob, u0, exact
 
 
-@pytest.mark.parametrize("inner", ["gmres", "bicgstab"])
+@pytest.mark.parametrize("inner", ["gmres", "bicgstab", "fft"])
 def test_fig1_advection_setup_1d(inner):
     """Fig. 1's discretisation (T = 0.0128, L = 64, M = 3, 5th-order upwind,
-    N = 700: not a power of two, so the inner solves are Krylov iterations on
-    the upwind stencil, GMRES at tau = 1e-15 as in the paper) in 1D: the whole
-    space-time solution against the sequential oracle and the last step
-    against the exact solution."""
+    N = 700) in 1D, with Krylov inner solves on the upwind stencil (GMRES at
+    tau = 1e-15 as in the paper, BiCGStab) and with the exact mixed-radix FFT
+    solve (700 = 7 * 5 * 5 * 4): the whole space-time solution against the
+    sequential oracle and the last step against the exact solution."""
     torch = torch_cuda()
     from paper_2103_12571_gb300.api import Plan
     prob, u0, exact = _advection(1, 700, 5, 3, 64, 0.0128)
@@ -115,13 +115,13 @@ def test_fig1_advection_setup_1d(inner):
     assert np.max(np.abs(u[-1, -1] - exact)) < 1e-12
 
 
-@pytest.mark.parametrize("inner", ["gmres", "bicgstab"])
+@pytest.mark.parametrize("inner", ["gmres", "bicgstab", "fft"])
 def test_fig1_advection_setup_2d(inner):
     """Fig. 1's setup in 2D, as the paper runs it: eq. (advection)
     u_t + u_x + u_y = 0 on the periodic unit square with N = 700^2 points,
     5th-order upwind stencils, L = 64, M = 3, T = 0.0128, Krylov inner solves
-    at tau = 1e-15 (GMRES, the paper's, and BiCGStab; 700 is not a power of
-    two).  All 192 blocks of the space-time solution against the Fourier
+    at tau = 1e-15 (GMRES, the paper's, and BiCGStab) or the exact
+    mixed-radix FFT solve.  All 192 blocks of the space-time solution against the Fourier
     closed form, the last step against the exact solution at 1e-12."""
     torch = torch_cuda()
     from paper_2103_12571_gb300.api import Plan
@@ -139,13 +139,13 @@ def test_fig1_advection_setup_2d(inner):
     assert np.max(np.abs(u[-1, -1].cpu().numpy() - exact)) < 1e-12, st
 
 
-@pytest.mark.parametrize("inner", ["gmres", "bicgstab"])
+@pytest.mark.parametrize("inner", ["gmres", "bicgstab", "fft"])
 @pytest.mark.parametrize("tol,N,order,M,L,tau", [(1e-5, 350, 2, 2, 8, 1e-8), (1e-9, 350, 4, 2, 16, 1e-11),
                                                  (1e-12, 600, 5, 3, 32, 1e-14)])
 def test_paper_advection_table1(tol, N, order, M, L, tau, inner):
     """Table 1's advection ladder (2D, T = 1e-2, N x N points, upwind of
     order kappa, GMRES (the paper's) or BiCGStab inner solves at the
-    table's tau): the paper's form of the iteration with Algorithm 2 and its
+    table's tau, or exact mixed-radix FFT solves): the paper's form of the iteration with Algorithm 2 and its
     last-step stop test.  The
     result is checked against the Fourier closed form of the collocation
     solution and against the exact solution at tol."""

@@ -21,6 +21,9 @@ CASES = [
     (workloads.problem(1, 512, cx=1.0, order=4, M=3, L=16, T=0.25), "c128"),
     (workloads.problem(2, 128, 128, nu=0.05, order=2, M=3, L=32, T=0.25), "c64"),
     (workloads.problem(2, 128, 256, nu=0.05, cx=0.5, cy=-0.25, order=2, M=3, L=8, T=0.0625), "c128"),
+    # mixed-radix solves (sizes that are not powers of two)
+    (workloads.problem(1, 700, cx=1.0, order=5, upwind=True, M=3, L=16, T=0.05), "c64"),
+    (workloads.problem(2, 45, 28, nu=0.02, cx=0.3, cy=-0.2, order=4, M=2, L=4, T=0.05), "c128"),
 ]
 
 
