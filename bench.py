@@ -404,7 +404,7 @@ def run_ours(args):
     # ---- headline: one FP64 Richardson iteration, inputs resident in HBM
     # (--mixed, for profiling captures only: the complex64 preconditioner)
     hprec = "c64" if args.mixed else "c128"
-    plan = Plan(prob, precision=hprec, alpha="paper", max_iter=60)
+    plan = Plan(prob, precision=hprec, alpha="paper", max_iter=60, space_cluster=args.space_cluster)
     alpha = correction_alpha(L, hprec)
     u = u0.repeat(L * M).reshape(L, M, N).contiguous()
     for _ in range(args.warmup):
@@ -703,6 +703,9 @@ def main():
                     help="only the timed steps (used for ncu captures): no e2e, time-to-tolerance or CPU legs")
     ap.add_argument("--mixed", action="store_true",
                     help="with --no-extras: time the mixed form's iteration instead (profiling captures)")
+    ap.add_argument("--space-cluster", type=int, default=0, choices=[0, 4, 8, 16],
+                    help="with --no-extras: the single-pass cluster spatial solve with this many CTAs per "
+                         "cluster (profiling captures; the default three passes measured faster)")
     ap.add_argument("--oracle-worker", type=int, default=0, help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.oracle_worker:
@@ -712,6 +715,8 @@ def main():
         args.warmup = 3
     if args.mixed and not args.no_extras:
         ap.error("--mixed is a profiling switch: use it with --no-extras")
+    if args.space_cluster and not args.no_extras:
+        ap.error("--space-cluster is a profiling switch: use it with --no-extras")
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -107,6 +107,12 @@ typedef struct {
     int form;           /* AC_FORM_CORRECTION | AC_FORM_PAPER                           */
     int inner_restart;  /* GMRES restart length m, 1..32 (<= 0: 30)                     */
     int update_kernel;  /* AC_UPDATE_PLAIN | AC_UPDATE_TMA                              */
+    int space_cluster;  /* 2D FFT solves of planes above 160 KB (power-of-two grids):
+                           0 or -1: three passes (rows, columns with the division, rows);
+                           4, 8, 16: one pass, each plane held in the shared memory of a
+                           thread-block cluster of that many CTAs (AC_ERR_INVALID_ARG if
+                           the cluster cannot hold a plane or does not fit on the device).
+                           The three passes measured faster on this GPU.                */
 } ac_alpha_schedule;
 
 /* Per-solve record (host memory, filled by the solve calls). */
@@ -130,12 +136,14 @@ typedef struct {
     int tile_fwd, tile_upd;           /* grid points per CTA in the time kernels        */
     int spatial_path;                 /* 0: 1D one CTA per plane, 1: 2D one CTA per plane, 2: 2D three passes,
                                          3: BiCGStab, 4: GMRES; 5: 1D mixed-radix FFT (sizes that are not
-                                         powers of two), one CTA per plane, 6: 2D mixed-radix three passes */
+                                         powers of two), one CTA per plane, 6: 2D mixed-radix three passes,
+                                         7: 2D in one pass over a thread-block cluster               */
     long long workspace_bytes;        /* device memory owned by the plan               */
     long long launches;               /* kernels launched by this plan so far          */
     int update_kernel;                /* AC_UPDATE_TMA if the TMA-staged update kernel is in use
                                          (requested and applicable), else AC_UPDATE_PLAIN   */
     int update_tile_tma;              /* grid points per tile of the TMA-staged kernel (0 if unused) */
+    int space_cluster;                /* spatial path 7: CTAs per cluster (else 0)      */
 } ac_plan_info;
 
 typedef struct ac_plan ac_plan;

@@ -38,7 +38,7 @@ class Schedule(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int), ("alpha0", ctypes.c_double), ("m0", ctypes.c_double),
                 ("tau", ctypes.c_double), ("max_iter", ctypes.c_int), ("stop_rule", ctypes.c_int),
                 ("inner_max_iter", ctypes.c_int), ("form", ctypes.c_int), ("inner_restart", ctypes.c_int),
-                ("update_kernel", ctypes.c_int)]
+                ("update_kernel", ctypes.c_int), ("space_cluster", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -54,7 +54,8 @@ class PlanInfo(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int), ("M", ctypes.c_int), ("L", ctypes.c_int), ("F", ctypes.c_int),
                 ("tile_fwd", ctypes.c_int), ("tile_upd", ctypes.c_int), ("spatial_path", ctypes.c_int),
                 ("workspace_bytes", ctypes.c_longlong), ("launches", ctypes.c_longlong),
-                ("update_kernel", ctypes.c_int), ("update_tile_tma", ctypes.c_int)]
+                ("update_kernel", ctypes.c_int), ("update_tile_tma", ctypes.c_int),
+                ("space_cluster", ctypes.c_int)]
 
 
 _P = ctypes.c_void_p

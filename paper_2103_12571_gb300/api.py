@@ -55,7 +55,7 @@ class Plan:
 
     def __init__(self, prob, M=None, L=None, dT=None, precision="c128", inner="fft", alpha="paper",
                  alpha0=1e-4, m0=0.0, tau=0.0, max_iter=50, stop="residual", inner_max_iter=0,
-                 form="correction", inner_restart=0, update_kernel="plain"):
+                 form="correction", inner_restart=0, update_kernel="plain", space_cluster=0):
         M = int(M if M is not None else prob["M"])
         L = int(L if L is not None else prob["L"])
         dT = float(dT if dT is not None else prob["T"] / L)
@@ -65,7 +65,7 @@ class Plan:
         sched = C.Schedule(mode=ALPHA[alpha], alpha0=float(alpha0), m0=float(m0), tau=float(tau),
                            max_iter=int(max_iter), stop_rule=STOP[stop], inner_max_iter=int(inner_max_iter),
                            form=FORM[form], inner_restart=int(inner_restart),
-                           update_kernel=UPDATE[update_kernel])
+                           update_kernel=UPDATE[update_kernel], space_cluster=int(space_cluster))
         handle = ctypes.c_void_p()
         C.check(C.lib().ac_setup(ctypes.byref(make_problem(prob)), M, L, dT, ctypes.byref(sched),
                                  PRECISION[precision], INNER[inner], ctypes.byref(handle)), "ac_setup")

@@ -76,6 +76,7 @@ struct ac_plan {
     int spatial_path;
     int rows_per_block, cols_per_block;
     ac::FftRadices rx, ry;   // radix plans of the mixed-radix FFT paths (5, 6)
+    int cluster;             // path 7: CTAs per cluster
     size_t csize;  // bytes per complex of the transform type
     // host data
     double t[8], Q[64];
@@ -271,9 +272,7 @@ static bool bicg_reliable(const ac_plan* p) { return p->spatial_path == 3 && p->
 // on `planes` planes of N complex values with per-plane shifts mu_dT, by the
 // plan's inner solver.  fetch_iters: copy the Krylov iteration counts to the
 // host (a stream-ordered copy; off inside graph capture).
-template <typename R>
-static int run_spatial(ac_plan* p, void* X, const void* mu_dT, int planes, int transposed, bool fetch_iters,
-                       cudaStream_t st, bool prof_passes = false) {
+static ac::SpaceArgs space_args(const ac_plan* p, void* X, const void* mu_dT, int planes, int transposed) {
     ac::SpaceArgs sa{};
     sa.nx = p->prob.nx;
     sa.ny = p->prob.dim == 2 ? p->prob.ny : 1;
@@ -291,6 +290,14 @@ static int run_spatial(ac_plan* p, void* X, const void* mu_dT, int planes, int t
     sa.cols_per_block = p->cols_per_block;
     sa.rx = p->rx;
     sa.ry = p->ry;
+    sa.cluster = p->cluster;
+    return sa;
+}
+
+template <typename R>
+static int run_spatial(ac_plan* p, void* X, const void* mu_dT, int planes, int transposed, bool fetch_iters,
+                       cudaStream_t st, bool prof_passes = false) {
+    const ac::SpaceArgs sa = space_args(p, X, mu_dT, planes, transposed);
     if (p->spatial_path == 0) {
         CK(ac::launch_space_1d<R>(sa, st));
         p->launches++;
@@ -312,6 +319,9 @@ static int run_spatial(ac_plan* p, void* X, const void* mu_dT, int planes, int t
             CK(ac::launch_space_rows<R>(sa, 1, st));
         }
         p->launches += 3;
+    } else if (p->spatial_path == 7) {
+        CK(ac::launch_space_cluster<R>(sa, st, nullptr));
+        p->launches++;
     } else if (p->spatial_path == 5) {
         CK(ac::launch_space_mr_1d<R>(sa, st));
         p->launches++;
@@ -1057,7 +1067,7 @@ int ac_setup(const ac_problem* prob, int M, int L, double dT, const ac_alpha_sch
     // spatial solve path and kernel tiles
     const size_t cs = p->csize;
     ac::PlanShape shape;
-    if (const char* why = ac::plan_shape(p->prob, M, L, precision, inner, sten.rad, &shape)) {
+    if (const char* why = ac::plan_shape(p->prob, M, L, precision, inner, sten.rad, sched->space_cluster, &shape)) {
         ac_destroy(p);
         return fail(AC_ERR_INVALID_ARG, "%s", why);
     }
@@ -1066,6 +1076,24 @@ int ac_setup(const ac_problem* prob, int M, int L, double dT, const ac_alpha_sch
     p->cols_per_block = shape.cols_per_block;
     p->rx = shape.rx;
     p->ry = shape.ry;
+    p->cluster = shape.cluster;
+    if (p->spatial_path == 7) {
+        // a cluster that the device cannot hold falls back to the three passes
+        int fits = 0;
+        const ac::SpaceArgs sa = space_args(p, nullptr, nullptr, 1, 0);
+        cudaError_t ce = precision == AC_C128 ? ac::launch_space_cluster<double>(sa, 0, &fits)
+                                              : ac::launch_space_cluster<float>(sa, 0, &fits);
+        if (ce != cudaSuccess || fits < 1) {
+            (void)cudaGetLastError();
+            if (sched->space_cluster > 0) {
+                ac_destroy(p);
+                return fail(AC_ERR_INVALID_ARG, "the requested cluster of %d CTAs does not fit on this device",
+                            sched->space_cluster);
+            }
+            p->spatial_path = 2;
+            p->cluster = 0;
+        }
+    }
     p->P = shape.P;
     p->grid = shape.grid;
     p->P_upd = shape.P_upd;
@@ -1183,6 +1211,7 @@ int ac_plan_get_info(const ac_plan* p, ac_plan_info* info) {
     info->launches = p->launches;
     info->update_kernel = p->tma_ok ? AC_UPDATE_TMA : AC_UPDATE_PLAIN;
     info->update_tile_tma = p->tma_ok ? p->tma_P : 0;
+    info->space_cluster = p->spatial_path == 7 ? p->cluster : 0;
     return AC_OK;
 }
 

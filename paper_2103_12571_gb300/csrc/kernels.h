@@ -78,6 +78,7 @@ struct SpaceArgs {
     const void* tw_y;            // [ny] twiddles
     int rows_per_block, cols_per_block;
     FftRadices rx, ry;           // radix plans of the mixed-radix (non-power-of-two) solves
+    int cluster;                 // CTAs per cluster of the single-pass 2D solve (4, 8, 16)
 };
 
 // BiCGStab on (I - dT mu A) x = X-plane with the stencil, tolerance tau.
@@ -161,6 +162,12 @@ template <typename R> cudaError_t launch_space_1d(const SpaceArgs& a, cudaStream
 template <typename R> cudaError_t launch_space_2d_small(const SpaceArgs& a, cudaStream_t st);
 template <typename R> cudaError_t launch_space_rows(const SpaceArgs& a, int inverse, cudaStream_t st);
 template <typename R> cudaError_t launch_space_cols(const SpaceArgs& a, cudaStream_t st);
+// Single-pass 2D solve, one plane per cluster of a.cluster CTAs.  With fits
+// non-null nothing is launched: *fits receives the number of clusters the
+// device can hold at once (0: the launch would fail).
+template <typename R> cudaError_t launch_space_cluster(const SpaceArgs& a, cudaStream_t st, int* fits);
+// shared memory per CTA of the single-pass 2D solve
+size_t space_cluster_smem(int nx, int ny, int cs, size_t csize);
 // Mixed-radix solves (grid sizes with prime factors 2, 3, 5, 7 only): one CTA
 // per 1D plane, and the row / column passes of the three-pass 2D solve.
 template <typename R> cudaError_t launch_space_mr_1d(const SpaceArgs& a, cudaStream_t st);

@@ -104,7 +104,7 @@ int run(const ac_problem* prob, int M, int L, double dT, double alpha, const dou
     if (!ac::problem_stencil(*prob, &sten)) return nfail(AC_ERR_INVALID_ARG, "unsupported stencil");
     // spatial path and kernel tiles: the ones ac_setup chooses for this problem
     ac::PlanShape sh;
-    if (const char* why = ac::plan_shape(*prob, M, L, precision, AC_INNER_FFT, sten.rad, &sh))
+    if (const char* why = ac::plan_shape(*prob, M, L, precision, AC_INNER_FFT, sten.rad, 0, &sh))
         return nfail(AC_ERR_INVALID_ARG, why);
 
     // carve the scratch array
@@ -217,12 +217,23 @@ int run(const ac_problem* prob, int M, int L, double dT, double alpha, const dou
     sa.cols_per_block = sh.cols_per_block;
     sa.rx = sh.rx;
     sa.ry = sh.ry;
+    sa.cluster = sh.cluster;
+    if (sh.spatial_path == 7) {
+        // as ac_setup: the three passes where the device cannot hold the clusters
+        int fits = 0;
+        if (ac::launch_space_cluster<R>(sa, st, &fits) != cudaSuccess || fits < 1) {
+            (void)cudaGetLastError();
+            sh.spatial_path = 2;
+        }
+    }
     if (sh.spatial_path == 0) chk(ac::launch_space_1d<R>(sa, st));
     else if (sh.spatial_path == 1) chk(ac::launch_space_2d_small<R>(sa, st));
     else if (sh.spatial_path == 2) {
         chk(ac::launch_space_rows<R>(sa, 0, st));
         chk(ac::launch_space_cols<R>(sa, st));
         chk(ac::launch_space_rows<R>(sa, 1, st));
+    } else if (sh.spatial_path == 7) {
+        chk(ac::launch_space_cluster<R>(sa, st, nullptr));
     } else if (sh.spatial_path == 5) {
         chk(ac::launch_space_mr_1d<R>(sa, st));
     } else {

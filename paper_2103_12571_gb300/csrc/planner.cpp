@@ -433,7 +433,18 @@ bool fft_radices(int n, FftRadices* o) {
     return n == 1;
 }
 
-const char* plan_shape(const ac_problem& prob, int M, int L, int precision, int inner, int rad, PlanShape* o) {
+// shared memory per CTA of the single-pass cluster solve (rows, x and y
+// tables, column twiddles), 0 if cs CTAs cannot hold a plane
+static size_t cluster_bytes(int nx, int ny, int cs, size_t csz) {
+    if (ny % cs || ny / cs < cs) return 0;
+    const size_t m = (size_t)ny / cs;
+    return csz * (m * nx + nx + 2 * m);
+}
+
+const char* plan_shape(const ac_problem& prob, int M, int L, int precision, int inner, int rad, int cluster_req,
+                       PlanShape* o) {
+    if (cluster_req != 0 && cluster_req != -1 && cluster_req != 4 && cluster_req != 8 && cluster_req != 16)
+        return "cluster size must be 0 or -1 (three passes), 4, 8 or 16";
     const int nx = prob.nx, ny = prob.dim == 2 ? prob.ny : 1;
     const long long N = (long long)nx * ny;
     const size_t cs = precision == AC_C128 ? 16 : 8;   // bytes per complex of the transform
@@ -480,6 +491,12 @@ const char* plan_shape(const ac_problem& prob, int M, int L, int precision, int 
             o->cols_per_block = W;
             if ((size_t)nx * cs > 160 * 1024 || (size_t)ny * W * cs > 160 * 1024)
                 return "2D grid too large for the three-pass FFT solve";
+            if (cluster_req == 4 || cluster_req == 8 || cluster_req == 16) {
+                const size_t b = cluster_bytes(nx, ny, cluster_req, cs);
+                if (b == 0 || b > 200 * 1024) return "the requested cluster cannot hold a plane";
+                o->spatial_path = 7;
+                o->cluster = cluster_req;
+            }
         }
     } else {
         o->spatial_path = inner == AC_INNER_GMRES ? 4 : 3;

@@ -59,8 +59,11 @@ struct PlanShape {
     int spatial_path;               // 0: 1D FFT, one CTA per plane; 1: 2D FFT, one CTA per plane;
                                     // 2: 2D FFT in three passes; 3: BiCGStab; 4: GMRES;
                                     // 5: 1D mixed-radix FFT, one CTA per plane; 6: 2D mixed-radix
-                                    // FFT in three passes (5, 6: sizes that are not powers of two)
-    int rows_per_block, cols_per_block;   // three-pass tiles
+                                    // FFT in three passes (5, 6: sizes that are not powers of two);
+                                    // 7: 2D FFT in one pass over a thread-block cluster
+    int rows_per_block, cols_per_block;   // three-pass tiles (also set for path 7, whose
+                                          // plans fall back to path 2 where the clusters do not fit)
+    int cluster;                    // path 7: CTAs per cluster
     FftRadices rx, ry;              // radix plans of paths 5 and 6
     int P, grid;                    // residual kernel: grid points per CTA, CTAs
     int P_upd, grid_upd;            // update kernel: grid points per CTA, CTAs
@@ -70,9 +73,13 @@ struct PlanShape {
 bool fft_radices(int n, FftRadices* out);
 
 // Null on success, else a message naming the unsupported size.  rad: the
-// stencil radius (Krylov paths need 2 rad + 1 points per axis).
+// stencil radius (Krylov paths need 2 rad + 1 points per axis).  cluster_req
+// (2D power-of-two FFT solves of planes above 160 KB): 4, 8 or 16 ask for the
+// single-pass solve over a cluster of that many CTAs (at most 200 KB of
+// shared memory each); 0 or -1 keep the three-pass solve, which measured
+// faster on every workload tried.
 const char* plan_shape(const ac_problem& prob, int M, int L, int precision, int inner, int rad,
-                       PlanShape* out);
+                       int cluster_req, PlanShape* out);
 
 // The alpha-dependent tables of one preconditioner (Lemma 1, eq. (QGL)):
 // per step l: s_l = alpha^{l/L}, qs_l = s_l dT Q (Q^T if transposed),
