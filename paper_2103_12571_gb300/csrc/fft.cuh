@@ -252,6 +252,65 @@ __device__ void fft_inv(C* data, int logn, int logb, int js, int bs, int ms, con
     }
 }
 
+// The last forward stage, a per-slot operation and the first inverse stage
+// in one pass: both stages work on blocks of 2^bits consecutive slots with
+// unit twiddles, so each thread transforms its block, replaces every output
+// v (slot `slot` of batch b) by op(v, slot, b) and transforms the block back.
+template <typename C, int R, bool BFAST, typename Op>
+__device__ __forceinline__ void fft_last_op_first(C* data, int logn, int logb, int js, int bs,
+                                                  const C* __restrict__ tw, Op op) {
+    constexpr int logR = R == 16 ? 4 : (R == 8 ? 3 : (R == 4 ? 2 : 1));
+    const int logitems_b = logn - logR;
+    const int total = 1 << (logitems_b + logb);
+    const auto one = tw[0].x;
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+        int b, i;
+        if (BFAST) {
+            b = t & ((1 << logb) - 1);
+            i = t >> logb;
+        } else {
+            i = t & ((1 << logitems_b) - 1);
+            b = t >> logitems_b;
+        }
+        const int base = i << logR;
+        C* p = data + (base * js + b * bs);
+        C v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = p[r * js];
+        small_dft<R, false>(v, one);
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = op(v[r], base + r, b);
+        small_dft<R, true>(v, one);
+#pragma unroll
+        for (int r = 0; r < R; ++r) p[r * js] = v[r];
+    }
+    __syncthreads();
+}
+
+// Forward transform, op on every slot of the spectrum (digit-reversed order,
+// see digitrev), inverse transform (not normalised): fft_fwd, a pass of op
+// and fft_inv with the two middle stages fused.  Ends with __syncthreads();
+// callers must synchronise before it.
+template <typename C, bool BFAST, int MAXB, typename Op>
+__device__ void fft_fwd_op_inv(C* data, int logn, int logb, int js, int bs, const C* __restrict__ tw, Op op) {
+    const int ns = fft_nstages<MAXB>(logn);
+    int logns = logn;
+    for (int s = 0; s < ns - 1; ++s) {
+        const int bits = fft_stage_bits<MAXB>(logn, s);
+        fft_stage_r<C, 1, false, BFAST, false, MAXB>(bits, data, logn, logns, logb, js, bs, 0, tw);
+        logns -= bits;
+    }
+    const int lb = fft_stage_bits<MAXB>(logn, ns - 1);
+    if (MAXB >= 4 && lb == 4) fft_last_op_first<C, (MAXB >= 4 ? 16 : 8), BFAST>(data, logn, logb, js, bs, tw, op);
+    else if (lb == 3) fft_last_op_first<C, 8, BFAST>(data, logn, logb, js, bs, tw, op);
+    else if (lb == 2) fft_last_op_first<C, 4, BFAST>(data, logn, logb, js, bs, tw, op);
+    else fft_last_op_first<C, 2, BFAST>(data, logn, logb, js, bs, tw, op);
+    for (int s = ns - 2; s >= 0; --s) {
+        const int bits = fft_stage_bits<MAXB>(logn, s);
+        fft_stage_r<C, 1, true, BFAST, false, MAXB>(bits, data, logn, logn - MAXB * s, logb, js, bs, 0, tw);
+    }
+}
+
 // ---- FP64 <-> FP32 on the integer pipe (the FP64 pipe of this GPU is narrow)
 
 // Round-to-nearest-even double -> float for the normal float range; values

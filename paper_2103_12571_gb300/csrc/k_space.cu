@@ -37,15 +37,11 @@ __global__ void __launch_bounds__(512) k_space_1d(SpaceArgs a) {
     __syncthreads();
     const C* tw = reinterpret_cast<const C*>(a.tw_x);
     const R one = tw[0].x;
-    fft_fwd<C, 1, false, SB>(d, logn, 0, 1, 0, 0, tw);
     const C mu = reinterpret_cast<const C*>(a.mu_dT)[blockIdx.x];
     const C* sig = reinterpret_cast<const C*>(a.sig_x);
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const int s = digitrev<SB>(i, logn);
-        d[s] = div_one_minus(d[s], cmul(mu, sig[i]), one);
-    }
-    __syncthreads();
-    fft_inv<C, 1, false, SB>(d, logn, 0, 1, 0, 0, tw);
+    fft_fwd_op_inv<C, false, SB>(d, logn, 0, 1, 0, tw, [&](C v, int slot, int) {
+        return div_one_minus(v, cmul(mu, sig[slot_freq<SB>(slot, logn)]), one);
+    });
     for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] = d[i];   // times n (not normalised)
 }
 
@@ -65,17 +61,13 @@ __global__ void __launch_bounds__(512) k_space_2d_small(SpaceArgs a) {
     const C* twy = reinterpret_cast<const C*>(a.tw_y);
     const R one = twx[0].x;
     fft_fwd<C, 1, false, SBX>(d, lx, ly, 1, nx, 0, twx);   // rows (x index fastest across threads)
-    fft_fwd<C, 1, true, SBY>(d, ly, lx, nx, 1, 0, twy);    // columns (column index fastest)
+    // columns (column index fastest): forward, divide, inverse
     const C mu = reinterpret_cast<const C*>(a.mu_dT)[blockIdx.x];
     const C* sx = reinterpret_cast<const C*>(a.sig_x);
     const C* sy = reinterpret_cast<const C*>(a.sig_y);
-    for (long i = threadIdx.x; i < N; i += blockDim.x) {
-        const int ky = (int)(i >> lx), kx = (int)(i & (nx - 1));
-        const long slot = ((long)digitrev<SBY>(ky, ly) << lx) + digitrev<SBX>(kx, lx);
-        d[slot] = div_one_minus(d[slot], cmul(mu, cadd(sx[kx], sy[ky])), one);
-    }
-    __syncthreads();
-    fft_inv<C, 1, true, SBY>(d, ly, lx, nx, 1, 0, twy);
+    fft_fwd_op_inv<C, true, SBY>(d, ly, lx, nx, 1, twy, [&](C v, int ys, int xs) {
+        return div_one_minus(v, cmul(mu, cadd(sx[slot_freq<SBX>(xs, lx)], sy[slot_freq<SBY>(ys, ly)])), one);
+    });
     fft_inv<C, 1, false, SBX>(d, lx, ly, 1, nx, 0, twx);
     for (long i = threadIdx.x; i < N; i += blockDim.x) x[i] = d[i];   // times N (not normalised)
 }
@@ -148,13 +140,8 @@ __global__ void __launch_bounds__(256) k_space_cols(SpaceArgs a) {
     }
     for (int i = threadIdx.x; i < ny; i += blockDim.x) my[i] = cmul(mu, sy[slot_freq<SBY>(i, a.logny)]);
     __syncthreads();
-    fft_fwd<C, 1, true, SBY>(d, a.logny, logW, W, 1, 0, twy);
-    for (long i = threadIdx.x; i < cnt; i += blockDim.x) {
-        const int ys = (int)(i >> logW), w = (int)(i & (W - 1));
-        d[i] = div_by(d[i], csub(mx[w], my[ys]), one);
-    }
-    __syncthreads();
-    fft_inv<C, 1, true, SBY>(d, a.logny, logW, W, 1, 0, twy);
+    fft_fwd_op_inv<C, true, SBY>(d, a.logny, logW, W, 1, twy,
+                                 [&](C v, int ys, int w) { return div_by(v, csub(mx[w], my[ys]), one); });
     for (long i = threadIdx.x; i < cnt; i += blockDim.x) {
         const int iy = (int)(i >> logW), w = (int)(i & (W - 1));
         x[(long)iy * nx + w] = d[i];
@@ -274,11 +261,9 @@ __global__ void __launch_bounds__(256) k_space_cluster(SpaceArgs a) {
     cl.sync();
     cluster_stage<C, CS, false>(cl, d, rank, m, nx, lx, twy);
     cl.sync();
-    fft_fwd<C, 1, true, SBY>(d, lm, lx, nx, 1, 0, twm);    // columns, local stages
-    for (int i = threadIdx.x; i < cnt; i += blockDim.x)
-        d[i] = div_by(d[i], csub(mx[i & (nx - 1)], my[i >> lx]), one);
-    __syncthreads();
-    fft_inv<C, 1, true, SBY>(d, lm, lx, nx, 1, 0, twm);
+    // columns, local stages: forward, divide, inverse
+    fft_fwd_op_inv<C, true, SBY>(d, lm, lx, nx, 1, twm,
+                                 [&](C v, int p, int xs) { return div_by(v, csub(mx[xs], my[p]), one); });
     cl.sync();
     cluster_stage<C, CS, true>(cl, d, rank, m, nx, lx, twy);
     cl.sync();   // no CTA reads another's shared memory after this point
