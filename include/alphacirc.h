@@ -208,6 +208,27 @@ int ac_richardson_step(ac_plan* plan, double alpha, const double* u0,
                        const double* b, double* u, double* res_rel_out,
                        void* stream);
 
+/* The same iteration on HOST arrays: u0 (N doubles, may be NULL), b (L*M*N
+ * doubles or NULL) and u (L*M*N doubles, in/out) live in host memory; the
+ * result equals ac_richardson_step's on device copies of them, bit for bit.
+ * The call copies u (and b) to the device and the new u back in `chunks`
+ * chunks of grid points (0: 8; at most 32; fewer when a chunk would be
+ * smaller than the stencil's halo), overlapping the copies with the
+ * residual and update kernels (eq. (Riteration)'s w - C u and u + e work
+ * point by point, apart from the halo).  The copies overlap only from
+ * page-locked host memory (cudaHostAlloc or cudaHostRegister); pageable
+ * memory works but is copied synchronously.  The first call allocates the
+ * plan's device copies of the arrays (L*M*N doubles each for u and b, N for
+ * u0) and two copy streams.  Returns after queueing the work, without
+ * waiting, unless res_rel_out is not NULL (as for ac_richardson_step); u is
+ * complete once the work queued on `stream` so far has finished (for
+ * example after cudaStreamSynchronize(stream)), and must not be touched by
+ * the host before that.  Errors: AC_ERR_INVALID_ARG (null plan or u,
+ * chunks < 0), AC_ERR_CUDA. */
+int ac_richardson_step_host(ac_plan* plan, double alpha, const double* u0,
+                            const double* b, double* u, int chunks,
+                            double* res_rel_out, void* stream);
+
 /* Full solve of C u = w by Richardson iterations with the plan's alpha
  * schedule (Algorithm 1 with Algorithm 2 or a fixed/mixed rule) and stop
  * rule; stops after at most sched.max_iter iterations.  If init_u is nonzero,

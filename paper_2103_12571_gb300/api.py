@@ -22,6 +22,14 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _host_ptr(t):
+    if t is None:
+        return None
+    if t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+        raise ValueError("expected a contiguous float64 CPU tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
 def _stream():
     return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
 
@@ -125,6 +133,19 @@ class Plan:
         C.check(C.lib().ac_richardson_step(self._h, float(alpha), _ptr(u0), _ptr(b), _ptr(u),
                                            ctypes.byref(res) if want_residual else None, _stream()),
                 "ac_richardson_step")
+        return res.value if want_residual else None
+
+    def richardson_step_host(self, alpha, u0, u, b=None, chunks=0, want_residual=False):
+        """ac_richardson_step on CPU tensors (u0: N doubles or None, u: L*M*N
+        doubles in/out, b: L*M*N doubles or None), copied in and out in
+        chunks that overlap the kernels (page-locked tensors for overlap).
+        Returns once the work is queued on the current stream (u is final
+        after it has run), or with the residual when want_residual."""
+        res = ctypes.c_double(0.0)
+        C.check(C.lib().ac_richardson_step_host(self._h, float(alpha), _host_ptr(u0), _host_ptr(b), _host_ptr(u),
+                                                int(chunks),
+                                                ctypes.byref(res) if want_residual else None, _stream()),
+                "ac_richardson_step_host")
         return res.value if want_residual else None
 
     def solve(self, u0, tol, b=None, u=None, raise_on_fail=True):

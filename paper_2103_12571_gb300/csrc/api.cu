@@ -66,6 +66,9 @@ struct EventPair {
     cudaEvent_t a, b;
 };
 
+// most chunks of ac_richardson_step_host's copy/compute pipeline
+static const int kHostChunks = 32;
+
 struct ac_plan {
     ac_problem prob;
     int M, L, logL, F, N, P, grid;
@@ -128,6 +131,15 @@ struct ac_plan {
     long long workspace = 0;
     long long launches = 0;
     cudaEvent_t ev_res = nullptr;
+    // ac_richardson_step_host: device copies of the host arrays, copy streams
+    // and the events that order copies and kernels (created on first use)
+    double* d_hu = nullptr;
+    double* d_hu0 = nullptr;
+    double* d_hb = nullptr;
+    cudaStream_t s_in = nullptr, s_out = nullptr;
+    cudaEvent_t ev_in[kHostChunks] = {};
+    cudaEvent_t ev_out[kHostChunks] = {};
+    cudaEvent_t ev_start = nullptr, ev_u0 = nullptr, ev_done = nullptr;
     // sequential stepping by diagonalisation of Q (ac_sequential_solve)
     double* d_seq_S = nullptr;      // [M][M] complex S, Q = S diag(lambda) S^{-1}
     double* d_seq_Sinv = nullptr;   // [M][M] complex S^{-1}
@@ -463,9 +475,8 @@ static void setup_tma(ac_plan* p) {
 
 // ------------------------------------------------------ one preconditioner
 // out (+)= C_alpha^{-1} (w - C u)   [u may be null: out (+)= C_alpha^{-1} w]
-template <typename R>
-static int stage_a(ac_plan* p, const double* u, const double* u0, const double* b, int b_rev, int transposed,
-                   cudaStream_t st, bool record_res, int recompute = 0, bool fwd_only = false) {
+static ac::FwdArgs fwd_args(const ac_plan* p, const double* u, const double* u0, const double* b, int b_rev,
+                           int transposed, int recompute) {
     ac::FwdArgs fa{};
     fa.g = transposed ? p->grid_adj : p->grid_fwd;
     fa.M = p->M;
@@ -487,6 +498,13 @@ static int stage_a(ac_plan* p, const double* u, const double* u0, const double* 
     fa.Sinv = p->d_Sinv;
     fa.X = p->X;
     fa.part = p->d_part_fwd;
+    return fa;
+}
+
+template <typename R>
+static int stage_a(ac_plan* p, const double* u, const double* u0, const double* b, int b_rev, int transposed,
+                   cudaStream_t st, bool record_res, int recompute = 0, bool fwd_only = false) {
+    const ac::FwdArgs fa = fwd_args(p, u, u0, b, b_rev, transposed, recompute);
     const size_t smem = (size_t)p->L * p->M * p->P * sizeof(R);
     {
         ProfScope ps(p, KK_FWD, st);
@@ -506,9 +524,7 @@ static int stage_a(ac_plan* p, const double* u, const double* u0, const double* 
     return AC_OK;
 }
 
-template <typename R>
-static int stage_b(ac_plan* p, double* out, int accumulate, cudaStream_t st, int diff_last = 0) {
-    const size_t smem = (size_t)p->L * p->M * p->P * sizeof(R);
+static ac::UpdArgs upd_args(const ac_plan* p, double* out, int accumulate, int diff_last) {
     ac::UpdArgs ua{};
     ua.N = p->N;
     ua.M = p->M;
@@ -524,6 +540,13 @@ static int stage_b(ac_plan* p, double* out, int accumulate, cudaStream_t st, int
     ua.accumulate = accumulate;
     ua.diff_last = diff_last;
     ua.part = p->d_part_upd;
+    return ua;
+}
+
+template <typename R>
+static int stage_b(ac_plan* p, double* out, int accumulate, cudaStream_t st, int diff_last = 0) {
+    const size_t smem = (size_t)p->L * p->M * p->P * sizeof(R);
+    ac::UpdArgs ua = upd_args(p, out, accumulate, diff_last);
     // the TMA-staged kernel for u += e on an aligned u (the map of u is
     // encoded once per u buffer)
     const bool tma = p->tma_ok && sizeof(R) == 4 && accumulate && !diff_last && ((uintptr_t)out & 15) == 0;
@@ -957,6 +980,151 @@ static int kry_alloc(ac_plan* p, int m) {
     return AC_OK;
 }
 
+// ------------------------------------------ one step on host buffers
+//
+// The iterate moves in and out in chunks of grid points (whole tiles of the
+// time kernels), each chunk a strided copy of L*M rows: the residual kernel
+// runs on a chunk as soon as the chunk and its stencil halo have landed, and
+// each chunk of the updated iterate goes back to the host while the update
+// kernel works on the next.  The kernels and their tiles are the device
+// step's, so the result is the same bit for bit.
+
+static int host_step_resources(ac_plan* p, bool with_b) {
+    cudaError_t e = cudaSuccess;
+    const size_t vec = sizeof(double) * (size_t)p->L * p->M * p->N;
+    if (!p->d_hu) {
+        e = dalloc(p, &p->d_hu, vec);
+        if (e != cudaSuccess) p->d_hu = nullptr;
+    }
+    if (e == cudaSuccess && !p->d_hu0) {
+        e = dalloc(p, &p->d_hu0, sizeof(double) * p->N);
+        if (e != cudaSuccess) p->d_hu0 = nullptr;
+    }
+    if (e == cudaSuccess && with_b && !p->d_hb) {
+        e = dalloc(p, &p->d_hb, vec);
+        if (e != cudaSuccess) p->d_hb = nullptr;
+    }
+    if (e == cudaSuccess && !p->s_in) e = cudaStreamCreateWithFlags(&p->s_in, cudaStreamNonBlocking);
+    if (e == cudaSuccess && !p->s_out) e = cudaStreamCreateWithFlags(&p->s_out, cudaStreamNonBlocking);
+    for (int c = 0; c < kHostChunks && e == cudaSuccess; ++c) {
+        if (!p->ev_in[c]) e = cudaEventCreateWithFlags(&p->ev_in[c], cudaEventDisableTiming);
+        if (e == cudaSuccess && !p->ev_out[c]) e = cudaEventCreateWithFlags(&p->ev_out[c], cudaEventDisableTiming);
+    }
+    for (cudaEvent_t* ev : {&p->ev_start, &p->ev_u0, &p->ev_done})
+        if (e == cudaSuccess && !*ev) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return fail(AC_ERR_CUDA, "host-step buffers: %s", cudaGetErrorString(e));
+    return AC_OK;
+}
+
+// Split `tiles` tiles of P points (N points in all) into at most `want`
+// chunks of whole tiles, boundaries t[0..K]; every chunk holds at least
+// `halo` points, else fewer chunks are used (K = 1 at worst).
+static int chunk_tiles(int tiles, int P, long N, long halo, int want, int* t) {
+    int K = std::max(1, std::min(std::min(want, kHostChunks), tiles));
+    const int T = (tiles + K - 1) / K;
+    K = (tiles + T - 1) / T;
+    if ((long)T * P < halo) K = 1;
+    for (int c = 0; c < K; ++c) t[c] = c * T;
+    t[K] = tiles;
+    while (K > 1 && std::min((long)t[K] * P, N) - (long)t[K - 1] * P < halo) t[--K] = tiles;
+    return K;
+}
+
+template <typename R>
+static int host_step(ac_plan* p, double alpha, const double* u0h, const double* bh, double* uh, double* res,
+                     int chunks, cudaStream_t st) {
+    const long N = p->N;
+    const size_t rows = (size_t)p->L * p->M, pitch = sizeof(double) * (size_t)N;
+    const long halo = (long)p->grid_fwd.rad * (p->prob.dim == 2 ? p->prob.nx : 1);
+    int tf[kHostChunks + 1], tu[kHostChunks + 1];
+    const int want = chunks > 0 ? chunks : 8;
+    const int Kf = chunk_tiles(p->grid, p->P, N, halo, want, tf);
+    const int Ku = chunk_tiles(p->grid_upd, p->P_upd, N, 0, want, tu);
+    const double* d_u0 = u0h ? p->d_hu0 : nullptr;
+    const double* d_b = bh ? p->d_hb : nullptr;
+
+    // copies in, after the work already queued on the caller's stream
+    CK(cudaEventRecord(p->ev_start, st));
+    CK(cudaStreamWaitEvent(p->s_in, p->ev_start, 0));
+    if (u0h) CK(cudaMemcpyAsync(p->d_hu0, u0h, sizeof(double) * N, cudaMemcpyHostToDevice, p->s_in));
+    CK(cudaEventRecord(p->ev_u0, p->s_in));
+    for (int c = 0; c < Kf; ++c) {
+        const long a = (long)tf[c] * p->P, e = std::min((long)tf[c + 1] * p->P, N);
+        CK(cudaMemcpy2DAsync(p->d_hu + a, pitch, uh + a, pitch, sizeof(double) * (e - a), rows,
+                             cudaMemcpyHostToDevice, p->s_in));
+        if (bh)
+            CK(cudaMemcpy2DAsync(p->d_hb + a, pitch, bh + a, pitch, sizeof(double) * (e - a), rows,
+                                 cudaMemcpyHostToDevice, p->s_in));
+        CK(cudaEventRecord(p->ev_in[c], p->s_in));
+    }
+
+    // ||w|| (for the reported residual) needs u0 and all of b before the first residual kernel
+    double wn2 = 1.0, winf = 1.0;
+    if (res) {
+        CK(cudaStreamWaitEvent(st, bh ? p->ev_in[Kf - 1] : p->ev_u0, 0));
+        int rc = w_norms(p, d_u0, d_b, &wn2, &winf, st);
+        if (rc) return rc;
+    }
+    const double wscale = res ? pow2_scale(winf) : (p->cur_wscale > 0 ? p->cur_wscale : 1.0);
+    int rc = ensure_tables(p, alpha, 0, wscale, st);
+    if (rc) return rc;
+
+    // residual + time FFT + node mix, chunk by chunk: chunk c needs chunks
+    // c - 1 and c + 1 for its stencil halo (periodic: chunk 0 needs the last)
+    ac::FwdArgs fa = fwd_args(p, p->d_hu, d_u0, d_b, 0, 0, 0);
+    const size_t smem_f = (size_t)p->L * p->M * p->P * sizeof(R);
+    CK(cudaStreamWaitEvent(st, p->ev_u0, 0));
+    auto fwd_chunk = [&](int c) -> cudaError_t {
+        fa.tile0 = tf[c];
+        p->launches++;
+        return ac::launch_fwd<R>(fa, tf[c + 1] - tf[c], smem_f, st);
+    };
+    if (Kf >= 3) {
+        for (int c = 1; c + 1 < Kf; ++c) {
+            CK(cudaStreamWaitEvent(st, p->ev_in[c + 1], 0));
+            CK(fwd_chunk(c));
+        }
+        CK(cudaStreamWaitEvent(st, p->ev_in[Kf - 1], 0));
+        CK(fwd_chunk(Kf - 1));
+        CK(fwd_chunk(0));
+    } else {
+        CK(cudaStreamWaitEvent(st, p->ev_in[Kf - 1], 0));
+        for (int c = 0; c < Kf; ++c) CK(fwd_chunk(c));
+    }
+    if (res) {
+        CK(cudaMemcpyAsync(p->h_part_fwd, p->d_part_fwd, sizeof(double) * p->grid, cudaMemcpyDeviceToHost, st));
+        CK(cudaEventRecord(p->ev_res, st));
+    }
+
+    rc = run_spatial<R>(p, p->X, p->d_mu, p->F * p->M, 0, true, st);
+    if (rc) return rc;
+
+    // update chunk by chunk; each chunk returns to the host while the next is updated
+    ac::UpdArgs ua = upd_args(p, p->d_hu, 1, 0);
+    const size_t smem_u = (size_t)p->L * p->M * p->P * sizeof(R);
+    for (int c = 0; c < Ku; ++c) {
+        ua.tile0 = tu[c];
+        CK(ac::launch_upd<R>(ua, tu[c + 1] - tu[c], smem_u, st));
+        p->launches++;
+        CK(cudaEventRecord(p->ev_out[c], st));
+        CK(cudaStreamWaitEvent(p->s_out, p->ev_out[c], 0));
+        const long a = (long)tu[c] * p->P_upd, e = std::min((long)tu[c + 1] * p->P_upd, N);
+        CK(cudaMemcpy2DAsync(uh + a, pitch, p->d_hu + a, pitch, sizeof(double) * (e - a), rows,
+                             cudaMemcpyDeviceToHost, p->s_out));
+    }
+    p->upd_grid_used = p->grid_upd;
+    // the caller's stream resumes after the last copy out
+    CK(cudaEventRecord(p->ev_done, p->s_out));
+    CK(cudaStreamWaitEvent(st, p->ev_done, 0));
+    if (res) {
+        CK(cudaEventSynchronize(p->ev_res));
+        double s = 0.0;
+        for (int i = 0; i < p->grid; ++i) s += p->h_part_fwd[i];
+        *res = wn2 > 0 ? std::sqrt(s) * (wscale / ac::kNormPrescale) / wn2 : std::sqrt(s) * (wscale / ac::kNormPrescale);
+    }
+    return AC_OK;
+}
+
 extern "C" {
 
 const char* ac_status_string(int s) {
@@ -994,6 +1162,16 @@ void ac_destroy(ac_plan* p) {
     for (void* b : {(void*)p->d_seq_S, (void*)p->d_seq_Sinv, p->d_seq_mu, (void*)p->d_kry, (void*)p->d_kpart})
         if (b) cudaFree(b);
     if (p->h_kpart) cudaFreeHost(p->h_kpart);
+    for (void* b : {(void*)p->d_hu, (void*)p->d_hu0, (void*)p->d_hb})
+        if (b) cudaFree(b);
+    for (int c = 0; c < kHostChunks; ++c) {
+        if (p->ev_in[c]) cudaEventDestroy(p->ev_in[c]);
+        if (p->ev_out[c]) cudaEventDestroy(p->ev_out[c]);
+    }
+    for (cudaEvent_t e : {p->ev_start, p->ev_u0, p->ev_done})
+        if (e) cudaEventDestroy(e);
+    if (p->s_in) cudaStreamDestroy(p->s_in);
+    if (p->s_out) cudaStreamDestroy(p->s_out);
     delete p;
 }
 
@@ -1275,6 +1453,17 @@ int ac_richardson_step(ac_plan* p, double alpha, const double* u0, const double*
         *res_rel_out = wn2 > 0 ? std::sqrt(s) * (wscale / ac::kNormPrescale) / wn2 : std::sqrt(s) * (wscale / ac::kNormPrescale);
     }
     return AC_OK;
+}
+
+int ac_richardson_step_host(ac_plan* p, double alpha, const double* u0, const double* b, double* u, int chunks,
+                            double* res_rel_out, void* stream) {
+    if (!p || !u) return fail(AC_ERR_INVALID_ARG, "null argument");
+    if (chunks < 0) return fail(AC_ERR_INVALID_ARG, "chunks must be >= 0");
+    int rc = host_step_resources(p, b != nullptr);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (p->precision == AC_C128) return host_step<double>(p, alpha, u0, b, u, res_rel_out, chunks, st);
+    return host_step<float>(p, alpha, u0, b, u, res_rel_out, chunks, st);
 }
 
 int ac_richardson_solve(ac_plan* p, const double* u0, const double* b, double* u, int init_u, double tol,

@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(256) k_fwd(FwdArgs a) {
     const int logP = 31 - __clz(P);
     const int L = a.L;
     const long N = a.g.N;
-    const long n0 = (long)blockIdx.x * P;
+    const long n0 = (long)(blockIdx.x + a.tile0) * P;
 
     __shared__ double coef_s[16];
     if (threadIdx.x < 16) {
@@ -256,7 +256,7 @@ __global__ void __launch_bounds__(256) k_fwd(FwdArgs a) {
         }
     }
     const double tot = block_sum_f2(sq, red);
-    if (threadIdx.x == 0) a.part[blockIdx.x] = tot;
+    if (threadIdx.x == 0) a.part[blockIdx.x + a.tile0] = tot;
 }
 
 template <typename R, int MM>
@@ -269,7 +269,7 @@ __global__ void __launch_bounds__(256) k_upd(UpdArgs a) {
     const int logP = 31 - __clz(P), logHP = logP - 1;
     const int L = a.L;
     const long N = a.N;
-    const long n0 = (long)blockIdx.x * P;
+    const long n0 = (long)(blockIdx.x + a.tile0) * P;
     const C* X = reinterpret_cast<const C*>(a.X);
     const C* Pm = reinterpret_cast<const C*>(a.Pm);
 
@@ -350,7 +350,7 @@ __global__ void __launch_bounds__(256) k_upd(UpdArgs a) {
     const unsigned long long mx = block_max_bits(emax, red);
     if (threadIdx.x == 0) {
         const double v = __longlong_as_double((long long)mx);
-        a.part[blockIdx.x] = a.diff_last ? v : v * a.sinv[L - 1];
+        a.part[blockIdx.x + a.tile0] = a.diff_last ? v : v * a.sinv[L - 1];
     }
 }
 

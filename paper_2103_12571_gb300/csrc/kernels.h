@@ -25,6 +25,7 @@ struct Grid {
 struct FwdArgs {
     Grid g;
     int M, L, logL, F, P;        // P grid points per block
+    int tile0;                   // first tile (block b works on tile tile0 + b; partial at part[tile0 + b])
     const double* u;             // L*M*N or null (then r = b)
     const double* u0;            // N or null: block-1 right-hand side
     const double* b;             // L*M*N or null: full right-hand side
@@ -45,6 +46,7 @@ struct FwdArgs {
 // (Gsubstitution), (s3)):  out_l (+)= sinv_l * IFFT_k( P_f X[f] )_l.
 struct UpdArgs {
     int N, M, L, logL, F, P;
+    int tile0;                   // first tile, as in FwdArgs (k_upd; k_upd_tma ignores it)
     const void* X;               // [F][M][N]
     const void* Pm;              // [F][M][M]
     const void* tw;              // L/2 twiddles
