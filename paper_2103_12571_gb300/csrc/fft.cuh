@@ -365,18 +365,24 @@ __device__ __forceinline__ double rcp_newton(double x, double one) {
 __device__ __forceinline__ float rcp_newton(float x, float) { return __frcp_rn(x); }
 
 // v / den: multiply by conj(den) / |den|^2 (den = 1 - mu sigma, with
-// |den| >= 1 whenever Re(mu sigma) <= 0; in any case far from 0 here).
+// |den| >= 1 whenever Re(mu sigma) <= 0; in any case far from 0 here).  In
+// FP64 every product and sum is an FMA with register operands (zero: a
+// register holding 0.0), as in the transforms.
 template <typename C, typename R>
-__device__ __forceinline__ C div_by(C v, C den, R one) {
-    const R inv = rcp_newton(fma(den.x, den.x, den.y * den.y), one);
-    return cscale(cmulc(v, den), inv);
+__device__ __forceinline__ C div_by(C v, C den, R one, R zero) {
+    if constexpr (sizeof(R) == 8) {
+        const R inv = rcp_newton(fma(den.x, den.x, fma(den.y, den.y, zero)), one);
+        const R px = fma(v.x, den.x, fma(v.y, den.y, zero));    // v * conj(den)
+        const R py = fma(v.y, den.x, fma(-v.x, den.y, zero));
+        return cmake(fma(px, inv, zero), fma(py, inv, zero));
+    } else {
+        const R inv = rcp_newton(fma(den.x, den.x, den.y * den.y), one);
+        return cscale(cmulc(v, den), inv);
+    }
 }
 template <typename C, typename R>
-__device__ __forceinline__ C div_one_minus(C v, C m, R one) {
-    C den;
-    den.x = one - m.x;
-    den.y = -m.y;
-    return div_by(v, den, one);
+__device__ __forceinline__ C div_one_minus(C v, C m, R one, R zero) {
+    return div_by(v, xsub(cmake(one, zero), m, one), one, zero);
 }
 
 }  // namespace ac

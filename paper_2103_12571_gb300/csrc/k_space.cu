@@ -36,11 +36,11 @@ __global__ void __launch_bounds__(512) k_space_1d(SpaceArgs a) {
     for (int i = threadIdx.x; i < n; i += blockDim.x) d[i] = x[i];
     __syncthreads();
     const C* tw = reinterpret_cast<const C*>(a.tw_x);
-    const R one = tw[0].x;
+    const R one = tw[0].x, zero = tw[0].y;
     const C mu = reinterpret_cast<const C*>(a.mu_dT)[blockIdx.x];
     const C* sig = reinterpret_cast<const C*>(a.sig_x);
     fft_fwd_op_inv<C, false, SB>(d, logn, 0, 1, 0, tw, [&](C v, int slot, int) {
-        return div_one_minus(v, cmul(mu, sig[slot_freq<SB>(slot, logn)]), one);
+        return div_one_minus(v, cmul(mu, sig[slot_freq<SB>(slot, logn)]), one, zero);
     });
     for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] = d[i];   // times n (not normalised)
 }
@@ -59,14 +59,14 @@ __global__ void __launch_bounds__(512) k_space_2d_small(SpaceArgs a) {
     __syncthreads();
     const C* twx = reinterpret_cast<const C*>(a.tw_x);
     const C* twy = reinterpret_cast<const C*>(a.tw_y);
-    const R one = twx[0].x;
+    const R one = twx[0].x, zero = twx[0].y;
     fft_fwd<C, 1, false, SBX>(d, lx, ly, 1, nx, 0, twx);   // rows (x index fastest across threads)
     // columns (column index fastest): forward, divide, inverse
     const C mu = reinterpret_cast<const C*>(a.mu_dT)[blockIdx.x];
     const C* sx = reinterpret_cast<const C*>(a.sig_x);
     const C* sy = reinterpret_cast<const C*>(a.sig_y);
     fft_fwd_op_inv<C, true, SBY>(d, ly, lx, nx, 1, twy, [&](C v, int ys, int xs) {
-        return div_one_minus(v, cmul(mu, cadd(sx[slot_freq<SBX>(xs, lx)], sy[slot_freq<SBY>(ys, ly)])), one);
+        return div_one_minus(v, cmul(mu, cadd(sx[slot_freq<SBX>(xs, lx)], sy[slot_freq<SBY>(ys, ly)])), one, zero);
     });
     fft_inv<C, 1, false, SBX>(d, lx, ly, 1, nx, 0, twx);
     for (long i = threadIdx.x; i < N; i += blockDim.x) x[i] = d[i];   // times N (not normalised)
@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(256) k_space_cols(SpaceArgs a) {
     const C* sx = reinterpret_cast<const C*>(a.sig_x);
     const C* sy = reinterpret_cast<const C*>(a.sig_y);
     const C* twy = reinterpret_cast<const C*>(a.tw_y);
-    const R one = twy[0].x;
+    const R one = twy[0].x, zero = twy[0].y;
     C* mx = d + cnt;                  // W entries: 1 - mu sigma_x of this tile's x slots
     C* my = mx + W;                   // ny entries: mu sigma_y per y slot
     for (int i = threadIdx.x; i < W; i += blockDim.x) {
@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(256) k_space_cols(SpaceArgs a) {
     for (int i = threadIdx.x; i < ny; i += blockDim.x) my[i] = cmul(mu, sy[slot_freq<SBY>(i, a.logny)]);
     __syncthreads();
     fft_fwd_op_inv<C, true, SBY>(d, a.logny, logW, W, 1, twy,
-                                 [&](C v, int ys, int w) { return div_by(v, csub(mx[w], my[ys]), one); });
+                                 [&](C v, int ys, int w) { return div_by(v, xsub(mx[w], my[ys], one), one, zero); });
     for (long i = threadIdx.x; i < cnt; i += blockDim.x) {
         const int iy = (int)(i >> logW), w = (int)(i & (W - 1));
         x[(long)iy * nx + w] = d[i];
@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(256) k_space_cluster(SpaceArgs a) {
     load_async16(d, x, (int)(cnt * sizeof(C) / 16));   // lands while the tables are formed
     const C* twx = reinterpret_cast<const C*>(a.tw_x);
     const C* twy = reinterpret_cast<const C*>(a.tw_y);
-    const R one = twx[0].x;
+    const R one = twx[0].x, zero = twx[0].y;
     const C mu = reinterpret_cast<const C*>(a.mu_dT)[plane];
     const C* sx = reinterpret_cast<const C*>(a.sig_x);
     const C* sy = reinterpret_cast<const C*>(a.sig_y);
@@ -263,7 +263,7 @@ __global__ void __launch_bounds__(256) k_space_cluster(SpaceArgs a) {
     cl.sync();
     // columns, local stages: forward, divide, inverse
     fft_fwd_op_inv<C, true, SBY>(d, lm, lx, nx, 1, twm,
-                                 [&](C v, int p, int xs) { return div_by(v, csub(mx[xs], my[p]), one); });
+                                 [&](C v, int p, int xs) { return div_by(v, xsub(mx[xs], my[p], one), one, zero); });
     cl.sync();
     cluster_stage<C, CS, true>(cl, d, rank, m, nx, lx, twy);
     cl.sync();   // no CTA reads another's shared memory after this point

@@ -152,7 +152,8 @@ __global__ void __launch_bounds__(256) k_space_mr_1d(SpaceArgs a) {
     C* d = mr_fft<C, false>(b0, b1, a.rx, n, 1, 1, 0, false, tw);
     const C mu = reinterpret_cast<const C*>(a.mu_dT)[blockIdx.x];
     const C* sig = reinterpret_cast<const C*>(a.sig_x);
-    for (int i = threadIdx.x; i < n; i += blockDim.x) d[i] = div_one_minus(d[i], cmul(mu, sig[i]), one);
+    const R zero = tw[0].y;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) d[i] = div_one_minus(d[i], cmul(mu, sig[i]), one, zero);
     __syncthreads();
     d = mr_fft<C, true>(d, d == b0 ? b1 : b0, a.rx, n, 1, 1, 0, false, tw);
     for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] = d[i];   // times n (not normalised)
@@ -208,7 +209,7 @@ __global__ void __launch_bounds__(256) k_space_mr_cols(SpaceArgs a) {
     const C* sx = reinterpret_cast<const C*>(a.sig_x);
     const C* sy = reinterpret_cast<const C*>(a.sig_y);
     const C* twy = reinterpret_cast<const C*>(a.tw_y);
-    const R one = twy[0].x;
+    const R one = twy[0].x, zero = twy[0].y;
     for (int i = threadIdx.x; i < wn; i += blockDim.x) {
         const C m = cmul(mu, sx[c0 + i]);
         mx[i] = cmake(one - m.x, -m.y);
@@ -218,7 +219,7 @@ __global__ void __launch_bounds__(256) k_space_mr_cols(SpaceArgs a) {
     C* d = mr_fft<C, false>(b0, b1, a.ry, ny, wn, wn, 1, true, twy);
     for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
         const int ky = i / wn, w = i - ky * wn;
-        d[i] = div_by(d[i], csub(mx[w], my[ky]), one);
+        d[i] = div_by(d[i], xsub(mx[w], my[ky], one), one, zero);
     }
     __syncthreads();
     d = mr_fft<C, true>(d, d == b0 ? b1 : b0, a.ry, ny, wn, wn, 1, true, twy);

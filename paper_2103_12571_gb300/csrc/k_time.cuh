@@ -226,7 +226,11 @@ __global__ void __launch_bounds__(256) k_fwd(FwdArgs a) {
 
     const C* Sinv = reinterpret_cast<const C*>(a.Sinv);
     C* X = reinterpret_cast<C*>(a.X);
-    const R half = (R)0.5;
+    // register copies of 0.5 and 0.0 (from the first twiddle, 1 - 0i): in
+    // FP64, h (a + b) = h a + h b exactly, written as two FMAs with register
+    // operands instead of an add and a multiply by a constant
+    const C w0 = reinterpret_cast<const C*>(a.tw)[0];
+    const R half = w0.x * (R)0.5, zero = w0.y;
     for (int idx = threadIdx.x; idx < a.F * HP; idx += blockDim.x) {
         const int k = idx >> logHP, q = idx & (HP - 1);
         const int pk = digitrev<3>(k, a.logL), pn = digitrev<3>((L - k) & (L - 1), a.logL);
@@ -236,14 +240,21 @@ __global__ void __launch_bounds__(256) k_fwd(FwdArgs a) {
         for (int m = 0; m < MM; ++m) {
             const C zk = Z[((long)pk * MM + m) * HP + q];
             const C zn = Z[((long)pn * MM + m) * HP + q];
-            A[m] = cmake(half * (zk.x + zn.x), realbin ? (R)0 : half * (zk.y - zn.y));
-            B[m] = cmake(half * (zk.y + zn.y), realbin ? (R)0 : half * (zn.x - zk.x));
+            if constexpr (sizeof(R) == 8) {
+                A[m] = cmake(fma(zk.x, half, fma(zn.x, half, zero)),
+                             realbin ? zero : fma(zk.y, half, fma(-zn.y, half, zero)));
+                B[m] = cmake(fma(zk.y, half, fma(zn.y, half, zero)),
+                             realbin ? zero : fma(zn.x, half, fma(-zk.x, half, zero)));
+            } else {
+                A[m] = cmake(half * (zk.x + zn.x), realbin ? (R)0 : half * (zk.y - zn.y));
+                B[m] = cmake(half * (zk.y + zn.y), realbin ? (R)0 : half * (zn.x - zk.x));
+            }
         }
         const C* S = Sinv + (long)k * MM * MM;
         const long nn = n0 + 2 * q;
 #pragma unroll
         for (int m = 0; m < MM; ++m) {
-            C xa = cmake((R)0, (R)0), xb = xa;
+            C xa = cmake(zero, zero), xb = xa;
 #pragma unroll
             for (int j = 0; j < MM; ++j) {
                 const C sm = S[m * MM + j];
@@ -273,6 +284,10 @@ __global__ void __launch_bounds__(256) k_upd(UpdArgs a) {
     const C* X = reinterpret_cast<const C*>(a.X);
     const C* Pm = reinterpret_cast<const C*>(a.Pm);
 
+    // register copies of 1.0 and 0.0 (first twiddle): in FP64 the sums and
+    // the first products below are FMAs with register operands only
+    const C w0 = reinterpret_cast<const C*>(a.tw)[0];
+    const R one = w0.x, zero = w0.y;
     for (int idx = threadIdx.x; idx < a.F * HP; idx += blockDim.x) {
         const int k = idx >> logHP, q = idx & (HP - 1);
         const long nn = n0 + 2 * q;
@@ -288,17 +303,17 @@ __global__ void __launch_bounds__(256) k_upd(UpdArgs a) {
         const int pk = digitrev<3>(k, a.logL), pn = digitrev<3>((L - k) & (L - 1), a.logL);
 #pragma unroll
         for (int m = 0; m < MM; ++m) {
-            C ya = cmake((R)0, (R)0), yb = ya;
+            C ya = cmake(zero, zero), yb = ya;
 #pragma unroll
             for (int j = 0; j < MM; ++j) {
                 const C pm = Pk[m * MM + j];
                 ya = cfma(pm, xa[j], ya);
                 yb = cfma(pm, xb[j], yb);
             }
-            if (realbin) { ya.y = (R)0; yb.y = (R)0; }
+            if (realbin) { ya.y = zero; yb.y = zero; }
             // Z_k = Y_a + i Y_b; Z_{L-k} = conj(Y_a) + i conj(Y_b)
-            Z[((long)pk * MM + m) * HP + q] = cmake(ya.x - yb.y, ya.y + yb.x);
-            if (!realbin) Z[((long)pn * MM + m) * HP + q] = cmake(ya.x + yb.y, yb.x - ya.y);
+            Z[((long)pk * MM + m) * HP + q] = cmake(fma(-yb.y, one, ya.x), fma(ya.y, one, yb.x));
+            if (!realbin) Z[((long)pn * MM + m) * HP + q] = cmake(fma(ya.x, one, yb.y), fma(-ya.y, one, yb.x));
         }
     }
     __syncthreads();
