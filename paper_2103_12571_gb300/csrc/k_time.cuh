@@ -138,7 +138,7 @@ __device__ __forceinline__ void residual_point(const FwdArgs& a, const RegCoef& 
 }
 
 template <typename R, int MM, int RAD, int DIM, bool GEN>
-__global__ void __launch_bounds__(256) k_fwd(FwdArgs a) {
+__global__ void __launch_bounds__(256, sizeof(R) == 8 ? 3 : 1) k_fwd(FwdArgs a) {
     typedef typename Cx<R>::T C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[32];
@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(256) k_fwd(FwdArgs a) {
 }
 
 template <typename R, int MM>
-__global__ void __launch_bounds__(256) k_upd(UpdArgs a) {
+__global__ void __launch_bounds__(256, sizeof(R) == 8 ? 3 : 1) k_upd(UpdArgs a) {
     typedef typename Cx<R>::T C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ unsigned long long red[32];
