@@ -138,7 +138,7 @@ struct ac_plan {
     double* d_hb = nullptr;
     cudaStream_t s_in = nullptr, s_out = nullptr;
     cudaEvent_t ev_in[kHostChunks] = {};
-    cudaEvent_t ev_out[kHostChunks] = {};
+    cudaEvent_t ev_out[kHostChunks + 4] = {};
     cudaEvent_t ev_start = nullptr, ev_u0 = nullptr, ev_done = nullptr;
     // sequential stepping by diagonalisation of Q (ac_sequential_solve)
     double* d_seq_S = nullptr;      // [M][M] complex S, Q = S diag(lambda) S^{-1}
@@ -983,11 +983,15 @@ static int kry_alloc(ac_plan* p, int m) {
 // ------------------------------------------ one step on host buffers
 //
 // The iterate moves in and out in chunks of grid points (whole tiles of the
-// time kernels), each chunk a strided copy of L*M rows: the residual kernel
-// runs on a chunk as soon as the chunk and its stencil halo have landed, and
-// each chunk of the updated iterate goes back to the host while the update
-// kernel works on the next.  The kernels and their tiles are the device
-// step's, so the result is the same bit for bit.
+// time kernels), each chunk a strided copy of L*M rows.  The copies in go in
+// the order: the stencil halo at the end of the grid (needed by chunk 0,
+// periodic), then each chunk followed by the halo at the start of the next
+// one, so that the residual kernel of chunk c can run as soon as chunk c and
+// that halo have landed.  Each chunk of the updated iterate goes back to the
+// host while the update kernel works on the next; the last update chunk is
+// split in four so that little is left to copy after the last kernel.  The
+// kernels and their tiles are the device step's, so the result is the same
+// bit for bit.
 
 static int host_step_resources(ac_plan* p, bool with_b) {
     cudaError_t e = cudaSuccess;
@@ -1006,10 +1010,10 @@ static int host_step_resources(ac_plan* p, bool with_b) {
     }
     if (e == cudaSuccess && !p->s_in) e = cudaStreamCreateWithFlags(&p->s_in, cudaStreamNonBlocking);
     if (e == cudaSuccess && !p->s_out) e = cudaStreamCreateWithFlags(&p->s_out, cudaStreamNonBlocking);
-    for (int c = 0; c < kHostChunks && e == cudaSuccess; ++c) {
+    for (int c = 0; c < kHostChunks && e == cudaSuccess; ++c)
         if (!p->ev_in[c]) e = cudaEventCreateWithFlags(&p->ev_in[c], cudaEventDisableTiming);
-        if (e == cudaSuccess && !p->ev_out[c]) e = cudaEventCreateWithFlags(&p->ev_out[c], cudaEventDisableTiming);
-    }
+    for (int c = 0; c < kHostChunks + 4 && e == cudaSuccess; ++c)
+        if (!p->ev_out[c]) e = cudaEventCreateWithFlags(&p->ev_out[c], cudaEventDisableTiming);
     for (cudaEvent_t* ev : {&p->ev_start, &p->ev_u0, &p->ev_done})
         if (e == cudaSuccess && !*ev) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
     if (e != cudaSuccess) return fail(AC_ERR_CUDA, "host-step buffers: %s", cudaGetErrorString(e));
@@ -1036,10 +1040,15 @@ static int host_step(ac_plan* p, double alpha, const double* u0h, const double* 
     const long N = p->N;
     const size_t rows = (size_t)p->L * p->M, pitch = sizeof(double) * (size_t)N;
     const long halo = (long)p->grid_fwd.rad * (p->prob.dim == 2 ? p->prob.nx : 1);
-    int tf[kHostChunks + 1], tu[kHostChunks + 1];
+    int tf[kHostChunks + 1], tu[kHostChunks + 4];
     const int want = chunks > 0 ? chunks : 8;
-    const int Kf = chunk_tiles(p->grid, p->P, N, halo, want, tf);
-    const int Ku = chunk_tiles(p->grid_upd, p->P_upd, N, 0, want, tu);
+    const int Kf = chunk_tiles(p->grid, p->P, N, 2 * halo, want, tf);
+    int Ku = chunk_tiles(p->grid_upd, p->P_upd, N, 0, want, tu);
+    if (Ku > 1 && tu[Ku] - tu[Ku - 1] >= 4) {   // the last update chunk in four
+        const int a0 = tu[Ku - 1], n = tu[Ku] - a0;
+        for (int i = 1; i <= 4; ++i) tu[Ku - 1 + i] = a0 + (int)((long)n * i / 4);
+        Ku += 3;
+    }
     const double* d_u0 = u0h ? p->d_hu0 : nullptr;
     const double* d_b = bh ? p->d_hb : nullptr;
 
@@ -1048,13 +1057,25 @@ static int host_step(ac_plan* p, double alpha, const double* u0h, const double* 
     CK(cudaStreamWaitEvent(p->s_in, p->ev_start, 0));
     if (u0h) CK(cudaMemcpyAsync(p->d_hu0, u0h, sizeof(double) * N, cudaMemcpyHostToDevice, p->s_in));
     CK(cudaEventRecord(p->ev_u0, p->s_in));
+    auto copy_in = [&](long a, long e) -> cudaError_t {
+        if (e <= a) return cudaSuccess;
+        cudaError_t ce = cudaMemcpy2DAsync(p->d_hu + a, pitch, uh + a, pitch, sizeof(double) * (e - a), rows,
+                                           cudaMemcpyHostToDevice, p->s_in);
+        if (ce == cudaSuccess && bh)
+            ce = cudaMemcpy2DAsync(p->d_hb + a, pitch, bh + a, pitch, sizeof(double) * (e - a), rows,
+                                   cudaMemcpyHostToDevice, p->s_in);
+        return ce;
+    };
+    // point ranges [beg, end) of the chunks; chunks hold at least 2 halo points
+    auto beg = [&](int c) { return (long)tf[c] * p->P; };
+    auto end = [&](int c) { return std::min((long)tf[c + 1] * p->P, N); };
+    const long h = Kf > 1 ? halo : 0;
+    CK(copy_in(N - h, N));                                   // halo of chunk 0 across the periodic seam
     for (int c = 0; c < Kf; ++c) {
-        const long a = (long)tf[c] * p->P, e = std::min((long)tf[c + 1] * p->P, N);
-        CK(cudaMemcpy2DAsync(p->d_hu + a, pitch, uh + a, pitch, sizeof(double) * (e - a), rows,
-                             cudaMemcpyHostToDevice, p->s_in));
-        if (bh)
-            CK(cudaMemcpy2DAsync(p->d_hb + a, pitch, bh + a, pitch, sizeof(double) * (e - a), rows,
-                                 cudaMemcpyHostToDevice, p->s_in));
+        const long a = c == 0 ? beg(c) : beg(c) + h;         // chunk c's first h points came earlier
+        const long e = c == Kf - 1 ? end(c) - h : end(c);    // the last h points came first
+        CK(copy_in(a, e));
+        if (c + 1 < Kf) CK(copy_in(beg(c + 1), beg(c + 1) + h));   // the halo at the start of the next chunk
         CK(cudaEventRecord(p->ev_in[c], p->s_in));
     }
 
@@ -1069,27 +1090,17 @@ static int host_step(ac_plan* p, double alpha, const double* u0h, const double* 
     int rc = ensure_tables(p, alpha, 0, wscale, st);
     if (rc) return rc;
 
-    // residual + time FFT + node mix, chunk by chunk: chunk c needs chunks
-    // c - 1 and c + 1 for its stencil halo (periodic: chunk 0 needs the last)
+    // residual + time FFT + node mix, chunk by chunk: ev_in[c] marks chunk c,
+    // the halo after it and (copied first) the halo before chunk 0 as landed;
+    // chunk c's halo before it lies in chunk c - 1 (or is that first copy)
     ac::FwdArgs fa = fwd_args(p, p->d_hu, d_u0, d_b, 0, 0, 0);
     const size_t smem_f = (size_t)p->L * p->M * p->P * sizeof(R);
     CK(cudaStreamWaitEvent(st, p->ev_u0, 0));
-    auto fwd_chunk = [&](int c) -> cudaError_t {
+    for (int c = 0; c < Kf; ++c) {
+        CK(cudaStreamWaitEvent(st, p->ev_in[c], 0));
         fa.tile0 = tf[c];
+        CK(ac::launch_fwd<R>(fa, tf[c + 1] - tf[c], smem_f, st));
         p->launches++;
-        return ac::launch_fwd<R>(fa, tf[c + 1] - tf[c], smem_f, st);
-    };
-    if (Kf >= 3) {
-        for (int c = 1; c + 1 < Kf; ++c) {
-            CK(cudaStreamWaitEvent(st, p->ev_in[c + 1], 0));
-            CK(fwd_chunk(c));
-        }
-        CK(cudaStreamWaitEvent(st, p->ev_in[Kf - 1], 0));
-        CK(fwd_chunk(Kf - 1));
-        CK(fwd_chunk(0));
-    } else {
-        CK(cudaStreamWaitEvent(st, p->ev_in[Kf - 1], 0));
-        for (int c = 0; c < Kf; ++c) CK(fwd_chunk(c));
     }
     if (res) {
         CK(cudaMemcpyAsync(p->h_part_fwd, p->d_part_fwd, sizeof(double) * p->grid, cudaMemcpyDeviceToHost, st));
@@ -1164,10 +1175,10 @@ void ac_destroy(ac_plan* p) {
     if (p->h_kpart) cudaFreeHost(p->h_kpart);
     for (void* b : {(void*)p->d_hu, (void*)p->d_hu0, (void*)p->d_hb})
         if (b) cudaFree(b);
-    for (int c = 0; c < kHostChunks; ++c) {
+    for (int c = 0; c < kHostChunks; ++c)
         if (p->ev_in[c]) cudaEventDestroy(p->ev_in[c]);
+    for (int c = 0; c < kHostChunks + 4; ++c)
         if (p->ev_out[c]) cudaEventDestroy(p->ev_out[c]);
-    }
     for (cudaEvent_t e : {p->ev_start, p->ev_u0, p->ev_done})
         if (e) cudaEventDestroy(e);
     if (p->s_in) cudaStreamDestroy(p->s_in);
