@@ -138,7 +138,7 @@ __device__ __forceinline__ void residual_point(const FwdArgs& a, const RegCoef& 
 }
 
 template <typename R, int MM, int RAD, int DIM, bool GEN>
-__global__ void __launch_bounds__(256, sizeof(R) == 8 ? 3 : 1) k_fwd(FwdArgs a) {
+__global__ void __launch_bounds__(256, sizeof(R) == 8 ? 3 : 0) k_fwd(FwdArgs a) {
     typedef typename Cx<R>::T C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[32];
@@ -226,11 +226,12 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 3 : 1) k_fwd(FwdArgs a) 
 
     const C* Sinv = reinterpret_cast<const C*>(a.Sinv);
     C* X = reinterpret_cast<C*>(a.X);
-    // register copies of 0.5 and 0.0 (from the first twiddle, 1 - 0i): in
-    // FP64, h (a + b) = h a + h b exactly, written as two FMAs with register
-    // operands instead of an add and a multiply by a constant
+    // in FP64, register copies of 0.5 and 0.0 (from the first twiddle,
+    // 1 - 0i): h (a + b) = h a + h b exactly, written as two FMAs with
+    // register operands instead of an add and a multiply by a constant.
+    // In FP32 literals.
     const C w0 = reinterpret_cast<const C*>(a.tw)[0];
-    const R half = w0.x * (R)0.5, zero = w0.y;
+    const R half = sizeof(R) == 8 ? w0.x * (R)0.5 : (R)0.5, zero = sizeof(R) == 8 ? w0.y : (R)0;
     for (int idx = threadIdx.x; idx < a.F * HP; idx += blockDim.x) {
         const int k = idx >> logHP, q = idx & (HP - 1);
         const int pk = digitrev<3>(k, a.logL), pn = digitrev<3>((L - k) & (L - 1), a.logL);
@@ -271,7 +272,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 3 : 1) k_fwd(FwdArgs a) 
 }
 
 template <typename R, int MM>
-__global__ void __launch_bounds__(256, sizeof(R) == 8 ? 3 : 1) k_upd(UpdArgs a) {
+__global__ void __launch_bounds__(256, sizeof(R) == 8 ? 3 : 0) k_upd(UpdArgs a) {
     typedef typename Cx<R>::T C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ unsigned long long red[32];
@@ -284,10 +285,11 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 3 : 1) k_upd(UpdArgs a) 
     const C* X = reinterpret_cast<const C*>(a.X);
     const C* Pm = reinterpret_cast<const C*>(a.Pm);
 
-    // register copies of 1.0 and 0.0 (first twiddle): in FP64 the sums and
-    // the first products below are FMAs with register operands only
+    // in FP64, register copies of 1.0 and 0.0 (first twiddle): the sums and
+    // the first products below are then FMAs with register operands only.
+    // In FP32 literals (registers would only raise the register count).
     const C w0 = reinterpret_cast<const C*>(a.tw)[0];
-    const R one = w0.x, zero = w0.y;
+    const R one = sizeof(R) == 8 ? w0.x : (R)1, zero = sizeof(R) == 8 ? w0.y : (R)0;
     for (int idx = threadIdx.x; idx < a.F * HP; idx += blockDim.x) {
         const int k = idx >> logHP, q = idx & (HP - 1);
         const long nn = n0 + 2 * q;
