@@ -212,10 +212,11 @@ int ac_richardson_step(ac_plan* plan, double alpha, const double* u0,
  * doubles or NULL) and u (L*M*N doubles, in/out) live in host memory; the
  * result equals ac_richardson_step's on device copies of them, bit for bit.
  * The call copies u (and b) to the device and the new u back in `chunks`
- * chunks of grid points (0: 8; at most 32; fewer when a chunk would be
- * smaller than the stencil's halo), overlapping the copies with the
+ * chunks of grid points (0: 8; at most 32; fewer when a chunk would hold
+ * less than twice the stencil's halo), overlapping the copies with the
  * residual and update kernels (eq. (Riteration)'s w - C u and u + e work
- * point by point, apart from the halo).  The copies overlap only from
+ * point by point, apart from the halo, whose points are copied ahead of the
+ * chunk that needs them).  The copies overlap only from
  * page-locked host memory (cudaHostAlloc or cudaHostRegister); pageable
  * memory works but is copied synchronously.  The first call allocates the
  * plan's device copies of the arrays (L*M*N doubles each for u and b, N for
