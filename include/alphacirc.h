@@ -361,6 +361,17 @@ int ac_freq_tables(int M, int L, double alpha, int transposed,
  * AC_ERR_INVALID_ARG for an unsupported scheme. */
 int ac_stencil_taps(const ac_problem* prob, double* tx, double* ty, int* rad);
 
+/* The launch shape ac_setup would choose for these arguments, computed on the
+ * host without a GPU: out->N, M, L, F, tile_fwd, tile_upd, spatial_path and
+ * space_cluster (the other fields are zero).  sched may be NULL (only its
+ * space_cluster field is read).  A requested cluster (spatial path 7) is
+ * reported as planned; ac_setup falls back to the three-pass solve, or fails
+ * for an explicit request, when the device cannot hold the clusters.
+ * Returns AC_ERR_INVALID_ARG for arguments ac_setup would reject (sizes,
+ * schemes, a grid the chosen inner solver cannot take). */
+int ac_plan_shape(const ac_problem* prob, int M, int L, int precision, int inner,
+                  const ac_alpha_schedule* sched, ac_plan_info* out);
+
 /* Algorithm 2's sequence: alphas[k] = alpha_{k+1}, ms[k] = m_k (ms[0] = m0),
  * k = 0..n-1 (ms has n+1 entries). */
 int ac_alpha_sequence(double m0, double gamma, int n, double* alphas, double* ms);

@@ -72,6 +72,7 @@ _PROTOS = {
     "ac_collocation_rhs": (_I, [_P, _P, _P, _P]),
     "ac_richardson_step": (_I, [_P, _D, _P, _P, _P, ctypes.POINTER(_D), _P]),
     "ac_richardson_step_host": (_I, [_P, _D, _P, _P, _P, _I, ctypes.POINTER(_D), _P]),
+    "ac_plan_shape": (_I, [ctypes.POINTER(Problem), _I, _I, _I, _I, ctypes.POINTER(Schedule), ctypes.POINTER(PlanInfo)]),
     "ac_richardson_solve": (_I, [_P, _P, _P, _P, _I, _D, ctypes.POINTER(Stats), _P]),
     "ac_adjoint_solve": (_I, [_P, _P, _P, _D, ctypes.POINTER(Stats), _P]),
     "ac_window_solve": (_I, [_P, _P, _I, _P, _P, _D, ctypes.POINTER(Stats), ctypes.POINTER(_I), _P]),

@@ -241,6 +241,18 @@ def stencil_taps(prob):
     return tx, ty, rad.value
 
 
+def plan_shape(prob, M=None, L=None, precision="c128", inner="fft", space_cluster=0):
+    """The launch shape ac_setup would choose (spatial path, time-kernel tiles,
+    cluster size), computed on the host without a GPU."""
+    M = int(M if M is not None else prob["M"])
+    L = int(L if L is not None else prob["L"])
+    sched = C.Schedule(space_cluster=int(space_cluster))
+    info = C.PlanInfo()
+    C.check(C.lib().ac_plan_shape(ctypes.byref(make_problem(prob)), M, L, PRECISION[precision], INNER[inner],
+                                  ctypes.byref(sched), ctypes.byref(info)), "ac_plan_shape")
+    return {f: getattr(info, f) for f, _ in C.PlanInfo._fields_}
+
+
 def collocation_matrix(M):
     Q = np.zeros(M * M)
     C.check(C.lib().ac_collocation_matrix(M, Q.ctypes.data_as(ctypes.c_void_p)), "ac_collocation_matrix")

@@ -571,6 +571,32 @@ extern "C" int ac_stencil_taps(const ac_problem* prob, double* tx, double* ty, i
     return AC_OK;
 }
 
+extern "C" int ac_plan_shape(const ac_problem* prob, int M, int L, int precision, int inner,
+                             const ac_alpha_schedule* sched, ac_plan_info* out) {
+    if (!prob || !out) return AC_ERR_INVALID_ARG;
+    if ((prob->dim != 1 && prob->dim != 2) || prob->nx < 2 || (prob->dim == 2 && prob->ny < 2) ||
+        !(prob->lx > 0) || (prob->dim == 2 && !(prob->ly > 0)))
+        return AC_ERR_INVALID_ARG;
+    if (M < 1 || M > 4 || L < 2 || L > 1024 || (L & (L - 1))) return AC_ERR_INVALID_ARG;
+    if (precision != AC_C128 && precision != AC_C64) return AC_ERR_INVALID_ARG;
+    if (inner != AC_INNER_FFT && inner != AC_INNER_BICGSTAB && inner != AC_INNER_GMRES) return AC_ERR_INVALID_ARG;
+    ac::Stencil st;
+    if (!ac::problem_stencil(*prob, &st)) return AC_ERR_INVALID_ARG;
+    ac::PlanShape sh;
+    if (ac::plan_shape(*prob, M, L, precision, inner, st.rad, sched ? sched->space_cluster : 0, &sh))
+        return AC_ERR_INVALID_ARG;
+    *out = ac_plan_info{};
+    out->N = prob->nx * (prob->dim == 2 ? prob->ny : 1);
+    out->M = M;
+    out->L = L;
+    out->F = L / 2 + 1;
+    out->tile_fwd = sh.P;
+    out->tile_upd = sh.P_upd;
+    out->spatial_path = sh.spatial_path;
+    out->space_cluster = sh.spatial_path == 7 ? sh.cluster : 0;
+    return AC_OK;
+}
+
 extern "C" int ac_radau_nodes(int M, double* t) {
     if (!t) return AC_ERR_INVALID_ARG;
     return ac::radau_nodes(M, t) ? AC_OK : AC_ERR_INVALID_ARG;

@@ -163,3 +163,63 @@ def test_binding_declares_every_header_function(api):
     binding (so no call goes through ctypes' default int conversions)."""
     from paper_2103_12571_gb300 import _lib
     assert sorted(declared_symbols()) == sorted(_lib._PROTOS)
+
+
+# ---- the planner's launch shapes (host logic, no GPU)
+def _shape(prob, **kw):
+    from paper_2103_12571_gb300.api import plan_shape
+    return plan_shape(prob, **kw)
+
+
+def test_plan_shape_spatial_paths():
+    """Power-of-two grids take the FFT paths 0 (1D), 1 (2D plane of at most
+    160 KB) and 2 (three passes); sizes with prime factors 2, 3, 5, 7 take the
+    mixed-radix paths 5 (1D) and 6 (2D); the Krylov solvers are paths 3 and 4;
+    the cluster solve (path 7) runs only on request."""
+    from paper_2103_12571_gb300 import workloads
+    P = workloads.problem
+    assert _shape(P(1, 4096, cx=1.0, order=4, M=3, L=256, T=1.0))["spatial_path"] == 0
+    assert _shape(P(2, 64, 64, nu=0.05, M=3, L=8, T=0.1))["spatial_path"] == 1
+    assert _shape(P(2, 512, 512, nu=1e-3, M=3, L=512, T=2.0))["spatial_path"] == 2
+    assert _shape(P(2, 512, 512, nu=1e-3, M=3, L=512, T=2.0), precision="c64")["spatial_path"] == 2
+    assert _shape(P(1, 700, cx=1.0, order=5, upwind=True, M=3, L=64, T=0.0128))["spatial_path"] == 5
+    assert _shape(P(2, 700, 700, cx=1.0, cy=1.0, order=5, upwind=True, M=3, L=64, T=0.0128))["spatial_path"] == 6
+    assert _shape(P(2, 350, 600, nu=0.01, M=2, L=8, T=0.01), precision="c64")["spatial_path"] == 6
+    prob = P(2, 24, 20, nu=0.02, M=3, L=8, T=0.1)
+    assert _shape(prob, inner="bicgstab")["spatial_path"] == 3
+    assert _shape(prob, inner="gmres")["spatial_path"] == 4
+    s = _shape(P(2, 256, 256, nu=0.05, M=3, L=64, T=0.5), precision="c64", space_cluster=8)
+    assert s["spatial_path"] == 7 and s["space_cluster"] == 8
+    assert _shape(P(2, 256, 256, nu=0.05, M=3, L=64, T=0.5), precision="c64")["space_cluster"] == 0
+
+
+def test_plan_shape_rejects_what_setup_rejects():
+    from paper_2103_12571_gb300 import workloads
+    from paper_2103_12571_gb300._lib import ACError
+    P = workloads.problem
+    for prob, kw in [
+        (P(1, 11 * 13, nu=0.1, M=2, L=8, T=0.1), {}),                          # prime factors 11, 13: no FFT
+        (P(2, 512, 64, nu=0.01, M=3, L=4, T=0.05), dict(precision="c64", space_cluster=16)),  # 4 rows per CTA
+        (P(2, 256, 256, nu=0.05, M=3, L=8, T=0.1), dict(space_cluster=5)),    # not a cluster size
+        (P(1, 64, nu=0.1, M=5, L=8, T=0.1), {}),                               # M > 4
+        (P(1, 64, nu=0.1, M=2, L=12, T=0.1), {}),                              # L not a power of two
+        (P(2, 2, 2, nu=0.1, order=6, M=2, L=8, T=0.1), dict(inner="bicgstab")),  # grid below the stencil
+    ]:
+        with pytest.raises(ACError):
+            _shape(prob, **kw)
+    # the same sizes with a Krylov inner solve are accepted
+    assert _shape(P(1, 11 * 13, nu=0.1, M=2, L=8, T=0.1), inner="gmres")["spatial_path"] == 4
+
+
+def test_plan_shape_time_tiles():
+    """Time-kernel tiles: L*M*P transform values within the shared-memory
+    budget (about 50 KB), at least two CTAs per SM where the grid allows, a
+    quarter or half tile for complex64 residual kernels."""
+    from paper_2103_12571_gb300 import workloads
+    prob = workloads.config(5)[0]
+    s128 = _shape(prob)
+    s64 = _shape(prob, precision="c64")
+    assert s128["tile_fwd"] == 4 and s128["F"] == 257 and s128["N"] == 512 * 512
+    assert s64["tile_fwd"] == 8
+    for s, rsz in ((s128, 8), (s64, 4)):
+        assert prob["L"] * prob["M"] * s["tile_fwd"] * rsz <= 50 * 1024
